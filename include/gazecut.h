@@ -1,0 +1,159 @@
+/*
+ * gazecut.h -- C ABI of the GB300 (sm_103a) exact min-cut for the gaze-line /
+ * depth-number stereo formulation of Oguri & Shibata, "A new stereo
+ * formulation not using pixel and disparity models" (arXiv 1803.01516).
+ *
+ * Pipeline (one stereo pair):
+ *   gs_stereo_cost_volume   data term g_v at every cross point        (§4.3, §3)
+ *   gs_build_graph          chain graph of the convex prior, with the
+ *                           terminal arcs folded into node excess     (§2 Eq. 1, §3, Fig. 4, §4.4)
+ *   gs_maxflow_solve        push-relabel with global relabelling      (§4.4)
+ *   gs_extract_labels       the cut as one depth number per gaze line (§3 "real cross points")
+ *
+ * Geometry.  The paper leaves the cuboid offsets out (§4.1); this library
+ * fixes them so that every cross point lies inside both images:
+ *   depth numbers S in [0, D), disparity dis(S) = dis0 - 2S, dis0 >= 2(D-1);
+ *   sites (gaze lines) W in [0, n_g), n_g = w - dis0, rows y in [0, h);
+ *   cross point (W, S, y) pairs right pixel x_r = W + S with left pixel
+ *   x_l = W + dis0 - S.
+ *
+ * Energy (§2, §3):  E(X) = sum_v C_v(X_v) + sum_(u,v) h~(X_u - X_v),
+ *   h~(d) = lambda |d| + inhibit (|d| - 1) [|d| > 1]
+ * over 4-connected sites; vertical pairs carry the inhibit term only when
+ * vertical_inhibit != 0.  The solve is exact: the flow value equals min E and
+ * the labels are the component-wise smallest minimiser (read from the
+ * minimal source set of the cut), so they do not depend on the schedule.
+ *
+ * Conventions shared by every call:
+ *   - All array pointers are DEVICE pointers owned by the caller unless a
+ *     parameter says "host".  The library allocates nothing; the caller sizes
+ *     buffers with the *_bytes() queries.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is stream-ordered and asynchronous unless stated.
+ *   - Host return value: GS_OK, GS_ERR_INVAL (bad sizes, NULL or misaligned
+ *     pointer; nothing was launched) or GS_ERR_CUDA (a launch failed).
+ *     Errors found on the device (overflow, non-converged solve) are written
+ *     to the caller's device status word instead, so no call needs a host
+ *     synchronisation.
+ *   - Device buffers must be 256-byte aligned (cudaMalloc / torch give this).
+ */
+#ifndef GAZECUT_H
+#define GAZECUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (host return values and device status words). */
+#define GS_OK            0
+#define GS_ERR_INVAL     1   /* bad argument; or a negative data cost seen on the device */
+#define GS_ERR_OVERFLOW  2   /* capacities / flow would not fit the int32 state */
+#define GS_ERR_TIMEOUT   3   /* max_iters reached before the cut was exact; state stays valid */
+#define GS_ERR_CUDA      4   /* a CUDA launch or copy failed */
+#define GS_ERR_LABELS    5   /* the cut was not one depth number per gaze line (internal check) */
+
+/* Problem description.  tau is used by the cost-volume call only. */
+typedef struct gs_params {
+    int32_t w, h;              /* image size in pixels (both images) */
+    int32_t D;                 /* number of depth numbers (labels), D >= 2 */
+    int32_t dis0;              /* disparity of depth number 0, dis0 >= 2(D-1), w - dis0 >= 1 */
+    int32_t tau;               /* truncation of the absolute-difference data term, >= 0 */
+    int32_t lambda;            /* penalty h~1 (smoothness), 0 <= lambda <= 2^28 */
+    int32_t inhibit;           /* inhibit h~2 (visibility), 0 <= inhibit <= 2^29 */
+    int32_t vertical_inhibit;  /* 1: inhibit on vertical pairs too; 0: horizontal pairs only */
+} gs_params;
+
+/* Solve modes. */
+#define GS_MODE_EXACT        0  /* iterate until no active node can reach the sink */
+#define GS_MODE_FIXED_SWEEPS 1  /* stop after fixed_sweeps local sweeps (approximate cut) */
+
+typedef struct gs_solve_opts {
+    int32_t mode;                /* GS_MODE_* */
+    int32_t sweeps_per_relabel;  /* local push-relabel sweeps between global relabels (>= 1) */
+    int32_t fixed_sweeps;        /* GS_MODE_FIXED_SWEEPS: total sweeps */
+    int32_t reserved;            /* must be 0 */
+    int64_t max_iters;           /* cap on global relabels in exact mode (> 0) */
+} gs_solve_opts;
+
+/* Derived sizes (0 when the params are invalid). */
+GS_API int32_t gs_num_sites_w(const gs_params *p);           /* n_g = w - dis0 */
+GS_API size_t  gs_cost_volume_bytes(const gs_params *p);     /* int32 [h][n_g][D] */
+GS_API size_t  gs_graph_bytes(const gs_params *p);           /* opaque solver state */
+GS_API size_t  gs_workspace_bytes(const gs_params *p, const gs_solve_opts *o);
+GS_API int64_t gs_num_nodes(const gs_params *p);             /* graph nodes without s, t: n_g*h*(D-1) */
+
+/*
+ * Data term g_v (§4.3, grayscale form, truncated as the workloads specify):
+ *   cost[(y*n_g + W)*D + S] = min(|L[y*pitch + W+dis0-S] - R[y*pitch + W+S]|, tau)
+ * L, R: uint8 images, row pitch `pitch` bytes (>= w).  cost: int32, layout
+ * [h][n_g][D] (one contiguous depth chain per site), gs_cost_volume_bytes().
+ */
+GS_API int gs_stereo_cost_volume(const uint8_t *L, const uint8_t *R, int32_t pitch, const gs_params *p,
+                          int32_t *cost, void *stream);
+
+/*
+ * Chain graph of §3 / Fig. 4 (Ishikawa construction for the convex h~ of Eq. 1):
+ *   chain node n(v, k), k in [1, D-1]; data arc n(v,k) -> n(v,k+1) carries
+ *   C_v(k) with an infinite reverse arc; penalty arcs u_k <-> v_k carry lambda;
+ *   inhibit arcs u_k -> v_(k-1), k >= 2, carry inhibit.  The source arc C_v(0)
+ *   and sink arc C_v(D-1) are folded into positive / negative node excess
+ *   (§4.4); heights start at 0.
+ * cost: int32 [h][n_g][D], every entry >= 0.  graph: gs_graph_bytes() bytes,
+ * written entirely.  status: device int32[1], set to GS_OK, GS_ERR_INVAL
+ * (negative cost) or GS_ERR_OVERFLOW (sum of source capacities > 2^30 or a
+ * cost > 2^30).
+ */
+GS_API int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t *status,
+                   void *stream);
+
+/*
+ * Max-flow on the graph state in place (§4.4): local push/relabel sweeps with
+ * a periodic global relabel (breadth-first distances to the remaining sink
+ * capacity), until no node with excess can reach the sink (GS_MODE_EXACT) or
+ * for a fixed number of sweeps (GS_MODE_FIXED_SWEEPS).
+ * workspace: gs_workspace_bytes() bytes of scratch, contents ignored on entry.
+ * status: device int32[1]; left as is when it already holds an error,
+ * otherwise set to GS_OK or GS_ERR_TIMEOUT (max_iters reached: the state is a
+ * valid preflow and the call can be repeated to continue) or GS_ERR_OVERFLOW.
+ */
+GS_API int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_opts *o, void *workspace,
+                     int32_t *status, void *stream);
+
+/*
+ * Labels and flow value from the solved state.
+ * GS_MODE_EXACT: S_min = nodes reachable from a node with positive excess in
+ *   the residual graph; labels[y*n_g + W] = |S_min ∩ chain(W, y)|, the
+ *   smallest minimiser of E.  flow = value of the maximum flow = min E.
+ * GS_MODE_FIXED_SWEEPS: the source side is the set of nodes that cannot reach
+ *   the sink (valid for any preflow); flow = flow routed so far (a lower
+ *   bound on min E).
+ * labels: int32 [h][n_g].  flow: device int64[1].  status as above
+ * (GS_ERR_LABELS if a chain's source side is not a prefix).
+ */
+GS_API int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, void *workspace,
+                      int32_t *labels, int64_t *flow, int32_t *status, void *stream);
+
+/* E(X) of §2 for labels int32 [h][n_g] over cost [h][n_g][D]; energy: device int64[1],
+ * negative if a label lies outside [0, D). */
+GS_API int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, int64_t *energy,
+              void *stream);
+
+/* Diagnostics of the last solve on this workspace: host int64[8] =
+ * {global relabels, sweeps, BFS passes, label passes, active nodes at exit,
+ *  0, 0, 0}.  Synchronises `stream`. */
+GS_API int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAZECUT_H */

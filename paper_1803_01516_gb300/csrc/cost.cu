@@ -1,0 +1,181 @@
+// Data term (§4.3), energy (§2) and the size queries of the C ABI.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+int make_geom(const gs_params *p, Geom *g) {
+    if (!p) return GS_ERR_INVAL;
+    if (p->w < 1 || p->h < 1 || p->D < 2) return GS_ERR_INVAL;
+    if (p->dis0 < 2 * (p->D - 1) || p->w - p->dis0 < 1) return GS_ERR_INVAL;
+    if (p->lambda < 0 || p->lambda > (1 << 28)) return GS_ERR_INVAL;
+    if (p->inhibit < 0 || p->inhibit > (1 << 29)) return GS_ERR_INVAL;
+    if (p->tau < 0) return GS_ERR_INVAL;
+    g->ng = p->w - p->dis0;
+    g->h = p->h;
+    g->D = p->D;
+    g->K = p->D - 1;
+    g->P = (int32_t)round_up(g->ng, 32);
+    g->SY = (int64_t)g->K * g->P;
+    g->N = (int64_t)g->h * g->SY;
+    g->lam = p->lambda;
+    g->lam2 = 2 * p->lambda;
+    g->h2h = p->inhibit;
+    g->h2v = p->vertical_inhibit ? p->inhibit : 0;
+    if (g->N > (int64_t)1 << 40) return GS_ERR_INVAL;
+    return GS_OK;
+}
+
+size_t graph_bytes(const Geom &g) {
+    return 256 + 9 * (size_t)round_up(g.N, 64) * sizeof(int32_t);
+}
+
+size_t work_bytes(const Geom &g) {
+    return 256 + (size_t)round_up(g.N, 64) * sizeof(int32_t);
+}
+
+State state_view(void *graph, const Geom &g) {
+    State s;
+    char *b = (char *)graph;
+    size_t stride = (size_t)round_up(g.N, 64) * sizeof(int32_t);
+    s.hdr = (GraphHeader *)b;
+    b += 256;
+    int32_t **arr[9] = {&s.rc, &s.rr, &s.rd, &s.ri0, &s.ri1, &s.ri2, &s.ri3, &s.ex, &s.ht};
+    for (int i = 0; i < 9; i++) *arr[i] = (int32_t *)(b + i * stride);
+    return s;
+}
+
+Work work_view(void *ws, const Geom &g) {
+    Work w;
+    w.ctrl = (Ctrl *)ws;
+    w.mark = (int32_t *)((char *)ws + 256);
+    return w;
+}
+
+// One block per (row y, tile of TW sites): the two image segments the tile
+// touches are staged in shared memory, then the [TW][D] output block, which is
+// contiguous in the cost volume, is written with coalesced stores.
+constexpr int kCostTW = 64;
+
+__global__ void k_cost_volume(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R,
+                              int pitch, int ng, int D, int dis0, int tau,
+                              int32_t *__restrict__ cost) {
+    extern __shared__ uint8_t sm[];
+    const int y = blockIdx.y;
+    const int W0 = blockIdx.x * kCostTW;
+    const int TW = min(kCostTW, ng - W0);
+    const int span = TW + D - 1;
+    uint8_t *sL = sm;            // L[y][W0 + dis0 - (D-1) + t]
+    uint8_t *sR = sm + span;     // R[y][W0 + t]
+    const uint8_t *Lrow = L + (size_t)y * pitch + (W0 + dis0 - (D - 1));
+    const uint8_t *Rrow = R + (size_t)y * pitch + W0;
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        sL[t] = Lrow[t];
+        sR[t] = Rrow[t];
+    }
+    __syncthreads();
+    int32_t *out = cost + ((size_t)y * ng + W0) * D;
+    const int n = TW * D;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int w = e / D, S = e - w * D;
+        // x_l = W + dis0 - S  ->  sL index w + (D-1) - S ; x_r = W + S -> sR index w + S
+        int d = (int)sL[w + (D - 1) - S] - (int)sR[w + S];
+        d = d < 0 ? -d : d;
+        out[e] = d < tau ? d : tau;
+    }
+}
+
+__device__ __forceinline__ long long pair_term(int a, int b, int lam, int inh) {
+    int d = a > b ? a - b : b - a;
+    return (long long)lam * d + (d > 1 ? (long long)inh * (d - 1) : 0);
+}
+
+__global__ void k_energy(const int32_t *__restrict__ cost, const int32_t *__restrict__ X, int ng,
+                         int h, int D, int lam, int h2h, int h2v,
+                         unsigned long long *__restrict__ out) {
+    long long acc = 0;
+    const long long n = (long long)ng * h;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int W = (int)(v % ng);
+        const int y = (int)(v / ng);
+        int a = X[v];
+        if (a < 0 || a >= D) {       // invalid label: flag the result (sign bit) and skip
+            atomicOr(out, 1ull << 63);
+            a = 0;
+        }
+        acc += cost[v * D + a];
+        if (W + 1 < ng) acc += pair_term(a, X[v + 1], lam, h2h);
+        if (y + 1 < h) acc += pair_term(a, X[v + ng], lam, h2v);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ long long red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(out, (unsigned long long)acc);
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+int32_t gs_num_sites_w(const gs_params *p) {
+    Geom g;
+    return make_geom(p, &g) == GS_OK ? g.ng : 0;
+}
+
+size_t gs_cost_volume_bytes(const gs_params *p) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK) return 0;
+    return (size_t)g.ng * g.h * g.D * sizeof(int32_t);
+}
+
+size_t gs_graph_bytes(const gs_params *p) {
+    Geom g;
+    return make_geom(p, &g) == GS_OK ? graph_bytes(g) : 0;
+}
+
+size_t gs_workspace_bytes(const gs_params *p, const gs_solve_opts *o) {
+    Geom g;
+    (void)o;
+    return make_geom(p, &g) == GS_OK ? work_bytes(g) : 0;
+}
+
+int64_t gs_num_nodes(const gs_params *p) {
+    Geom g;
+    return make_geom(p, &g) == GS_OK ? (int64_t)g.ng * g.h * g.K : 0;
+}
+
+int gs_stereo_cost_volume(const uint8_t *L, const uint8_t *R, int32_t pitch, const gs_params *p,
+                          int32_t *cost, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !L || !R || !cost || pitch < p->w) return GS_ERR_INVAL;
+    dim3 grid((g.ng + kCostTW - 1) / kCostTW, g.h);
+    size_t smem = 2 * (size_t)(kCostTW + g.D - 1);
+    if (smem > 48 * 1024) return GS_ERR_INVAL;
+    k_cost_volume<<<grid, 256, smem, (cudaStream_t)stream>>>(L, R, pitch, g.ng, g.D, p->dis0,
+                                                             p->tau, cost);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, int64_t *energy,
+              void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !cost || !labels || !energy) return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemsetAsync(energy, 0, sizeof(int64_t), st));
+    long long sites = (long long)g.ng * g.h;
+    int blocks = (int)std::min<long long>((sites + 255) / 256, 4 * 152);
+    k_energy<<<blocks, 256, 0, st>>>(cost, labels, g.ng, g.h, g.D, g.lam, g.h2h, g.h2v,
+                                     (unsigned long long *)energy);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// Graph construction (§3 / Fig. 4, terminals folded as in §4.4) and reading
+// the cut back as labels (§3 "real cross points").
+#include "arcs.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ void block_sum_u64(unsigned long long v, unsigned long long *out) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ unsigned long long red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(out, v);
+    }
+}
+
+__global__ void k_header(GraphHeader *hdr, Geom g, int inhibit, int vinhibit) {
+    hdr->magic = kMagic;
+    hdr->D = g.D;
+    hdr->ng = g.ng;
+    hdr->h = g.h;
+    hdr->K = g.K;
+    hdr->P = g.P;
+    hdr->lam = g.lam;
+    hdr->inhibit = inhibit;
+    hdr->vinhibit = vinhibit;
+    hdr->base_flow = 0;
+    hdr->init_deficit = 0;
+    hdr->src_total = 0;
+    hdr->max_cost = 0;
+}
+
+// One thread per node.  Chain node j = k-1 of site (W, y):
+//   rc  = C(k) for the data arc n_k -> n_(k+1), k in [1, D-2]
+//   ex  = C(0) at k = 1 (folded source arc) minus C(D-1) at k = D-1 (folded
+//         sink arc); with D = 2 both fold into the same node and min(C0, C1)
+//         flows s -> n -> t directly (base flow)
+//   penalty residuals start at lambda (no flow), inhibit residuals at h2.
+__global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t *status) {
+    unsigned long long base = 0, deficit = 0, src = 0;
+    int bad = 0, big = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const NodePos p = node_pos(g, i);
+        if (p.W >= g.ng) {
+            s.rc[i] = s.rr[i] = s.rd[i] = 0;
+            s.ri0[i] = s.ri1[i] = s.ri2[i] = s.ri3[i] = 0;
+            s.ex[i] = 0;
+            s.ht[i] = kInfH;
+            continue;
+        }
+        const int32_t *c = C + ((int64_t)p.y * g.ng + p.W) * g.D;
+        const int k = p.j + 1;
+        int32_t ck = c[k];
+        int32_t rc = (p.j < g.K - 1) ? ck : 0;
+        int64_t e = 0;
+        if (p.j == 0) {
+            const int32_t c0 = c[0];
+            bad |= c0 < 0;
+            big |= c0 > kCapLimit;
+            e += c0;
+            src += (unsigned long long)max(c0, 0);
+        }
+        bad |= ck < 0;
+        big |= ck > kCapLimit;
+        if (p.j == g.K - 1) {
+            e -= c[g.D - 1];
+            if (g.K == 1) base += (unsigned long long)max(min(c[0], c[1]), 0);
+            if (e < 0) deficit += (unsigned long long)(-e);
+        }
+        s.rc[i] = rc;
+        s.ex[i] = (int32_t)e;
+        s.rr[i] = (p.W < g.ng - 1) ? g.lam : 0;
+        s.rd[i] = (p.y < g.h - 1) ? g.lam : 0;
+        const bool dn = p.j > 0;
+        s.ri0[i] = (dn && p.W > 0) ? g.h2h : 0;
+        s.ri1[i] = (dn && p.W < g.ng - 1) ? g.h2h : 0;
+        s.ri2[i] = (dn && p.y > 0) ? g.h2v : 0;
+        s.ri3[i] = (dn && p.y < g.h - 1) ? g.h2v : 0;
+        s.ht[i] = 0;
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_INVAL);
+    }
+    if (__syncthreads_or(big)) {
+        if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_OVERFLOW);
+    }
+    block_sum_u64(base, &s.hdr->base_flow);
+    block_sum_u64(deficit, &s.hdr->init_deficit);
+    block_sum_u64(src, &s.hdr->src_total);
+}
+
+__global__ void k_check_totals(const GraphHeader *hdr, int32_t *status) {
+    if (hdr->src_total > (unsigned long long)kCapLimit ||
+        hdr->init_deficit > (unsigned long long)kCapLimit)
+        atomicCAS(status, GS_OK, GS_ERR_OVERFLOW);
+}
+
+// ---------------------------------------------------------------- labels ---
+
+// S_min seed: nodes with positive excess.
+__global__ void k_mark_init(Geom g, State s, int32_t *mark) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int W = (int)(i % g.P);
+        mark[i] = (W < g.ng && s.ex[i] > 0) ? 1 : 0;
+    }
+}
+
+// One pass of forward reachability: a marked node marks every head of a
+// residual arc.  Writes are idempotent, so passes need no atomics.
+__global__ void k_mark_pass(Geom g, State s, int32_t *mark, Ctrl *ctrl) {
+    int changed = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!mark[i]) continue;
+        const NodePos p = node_pos(g, i);
+        if (p.W >= g.ng) continue;
+        int32_t r[kSlots];
+        load_residuals(s, g, i, p, r);
+#pragma unroll
+        for (int q = 0; q < kSlots; q++) {
+            if (r[q] > 0) {
+                const int64_t v = i + slot_offset(g, q);
+                if (!mark[v]) {
+                    mark[v] = 1;
+                    changed = 1;
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicExch(&ctrl->changed, 1);
+}
+
+// labels[y][W] = number of source-side nodes of the chain; the source side
+// must be a prefix of the chain (mode 0: mark != 0, mode 1: ht == inf).
+__global__ void k_labels(Geom g, State s, const int32_t *mark, int use_heights, int32_t *labels,
+                         int32_t *status) {
+    const int64_t sites = (int64_t)g.ng * g.h;
+    int bad = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < sites;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int W = (int)(v % g.ng), y = (int)(v / g.ng);
+        int64_t i = (int64_t)y * g.SY + W;
+        int a = 0, prev = 1;
+        for (int j = 0; j < g.K; j++, i += g.P) {
+            const int in = use_heights ? (s.ht[i] >= kInfH) : (mark[i] != 0);
+            bad |= in && !prev;
+            a += in;
+            prev = in;
+        }
+        labels[v] = a;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_LABELS);
+}
+
+__global__ void k_deficit(Geom g, State s, unsigned long long *out) {
+    unsigned long long d = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = s.ex[i];
+        if (e < 0) d += (unsigned long long)(-(int64_t)e);
+    }
+    block_sum_u64(d, out);
+}
+
+__global__ void k_flow(const GraphHeader *hdr, const Ctrl *ctrl, int64_t *flow) {
+    *flow = (int64_t)hdr->base_flow + (int64_t)hdr->init_deficit - (int64_t)ctrl->deficit_left;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+static int grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+// Shared with solve.cu: run the global relabel to convergence (defined there).
+namespace gs {
+int global_relabel(const Geom &g, const State &s, const Work &w, cudaStream_t st, int64_t *passes);
+}
+
+extern "C" {
+
+int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t *status,
+                   void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !cost || !graph || !status) return GS_ERR_INVAL;
+    if (((uintptr_t)graph & 255) != 0) return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    State s = state_view(graph, g);
+    GS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    k_header<<<1, 1, 0, st>>>(s.hdr, g, p->inhibit, p->vertical_inhibit);
+    k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
+    k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, void *workspace,
+                      int32_t *labels, int64_t *flow, int32_t *status, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !o || !graph || !workspace || !labels || !flow || !status)
+        return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    State s = state_view(graph, g);
+    Work w = work_view(workspace, g);
+    const int grid = grid_for(g.N);
+    if (o->mode == GS_MODE_EXACT) {
+        k_mark_init<<<grid, 256, 0, st>>>(g, s, w.mark);
+        int64_t passes = 0;
+        for (;;) {
+            GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->changed, 0, sizeof(int32_t), st));
+            k_mark_pass<<<grid, 256, 0, st>>>(g, s, w.mark, w.ctrl);
+            int32_t changed = 0;
+            GS_CUDA_TRY(cudaMemcpyAsync(&changed, &w.ctrl->changed, sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, st));
+            GS_CUDA_TRY(cudaStreamSynchronize(st));
+            passes++;
+            if (!changed) break;
+        }
+        long long lp = passes;
+        GS_CUDA_TRY(cudaMemcpyAsync(&w.ctrl->stats[3], &lp, sizeof(long long),
+                                    cudaMemcpyHostToDevice, st));
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        k_labels<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(g, s, w.mark, 0, labels, status);
+    } else {
+        int64_t passes = 0;
+        int rc = global_relabel(g, s, w, st, &passes);
+        if (rc) return rc;
+        k_labels<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(g, s, w.mark, 1, labels, status);
+    }
+    GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->deficit_left, 0, sizeof(unsigned long long), st));
+    k_deficit<<<grid, 256, 0, st>>>(g, s, &w.ctrl->deficit_left);
+    k_flow<<<1, 1, 0, st>>>(s.hdr, w.ctrl, flow);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stream) {
+    if (!workspace || !host_stats) return GS_ERR_INVAL;
+    const Ctrl *c = (const Ctrl *)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemcpyAsync(host_stats, c->stats, 8 * sizeof(long long),
+                                cudaMemcpyDeviceToHost, st));
+    GS_CUDA_TRY(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+}  // extern "C"

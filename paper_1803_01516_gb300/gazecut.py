@@ -1,0 +1,249 @@
+"""Python binding of the C ABI in ``include/gazecut.h`` (argument marshalling only).
+
+Every function with a ``gs_`` name calls the C entry point of the same name in
+``libgazecut.so``: it checks dtypes, devices and sizes, passes the tensors'
+device pointers and the current CUDA stream, and raises on a non-zero host
+status.  No step of the method runs here; torch only provides device memory
+and streams.  The library must have been built (``__graft_entry__.build()``);
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgazecut.so")
+
+GS_OK, GS_ERR_INVAL, GS_ERR_OVERFLOW, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_LABELS = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "OVERFLOW", 3: "TIMEOUT", 4: "CUDA", 5: "LABELS"}
+GS_MODE_EXACT, GS_MODE_FIXED_SWEEPS = 0, 1
+
+EXPORTS = [
+    "gs_num_sites_w", "gs_cost_volume_bytes", "gs_graph_bytes", "gs_workspace_bytes",
+    "gs_num_nodes", "gs_stereo_cost_volume", "gs_build_graph", "gs_maxflow_solve",
+    "gs_extract_labels", "gs_energy", "gs_solve_stats",
+]
+
+
+class GsParams(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("dis0", ctypes.c_int32), ("tau", ctypes.c_int32), ("lambda_", ctypes.c_int32),
+                ("inhibit", ctypes.c_int32), ("vertical_inhibit", ctypes.c_int32)]
+
+
+class GsSolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("sweeps_per_relabel", ctypes.c_int32),
+                ("fixed_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_iters", ctypes.c_int64)]
+
+
+@dataclass
+class Params:
+    """Problem description (mirrors ``gs_params``)."""
+
+    w: int
+    h: int
+    D: int
+    tau: int
+    lam: int
+    inhibit: int = 1023
+    vertical_inhibit: int = 1
+    dis0: int | None = None      # default 2(D-1): depth covers disparities 0..2(D-1)
+
+    def c(self) -> GsParams:
+        dis0 = 2 * (self.D - 1) if self.dis0 is None else self.dis0
+        return GsParams(self.w, self.h, self.D, dis0, self.tau, self.lam, self.inhibit,
+                        self.vertical_inhibit)
+
+    @property
+    def ng(self) -> int:
+        return self.w - (2 * (self.D - 1) if self.dis0 is None else self.dis0)
+
+
+@dataclass
+class SolveOpts:
+    """Solver options (mirrors ``gs_solve_opts``)."""
+
+    mode: int = GS_MODE_EXACT
+    sweeps_per_relabel: int = 8
+    fixed_sweeps: int = 0
+    max_iters: int = 1 << 16
+
+    def c(self) -> GsSolveOpts:
+        return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, 0, self.max_iters)
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libgazecut.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first "
+                               "(the CUDA library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        pp = ctypes.POINTER(GsParams)
+        po = ctypes.POINTER(GsSolveOpts)
+        sig = {
+            "gs_num_sites_w": ([pp], I32),
+            "gs_cost_volume_bytes": ([pp], SZ),
+            "gs_graph_bytes": ([pp], SZ),
+            "gs_workspace_bytes": ([pp, po], SZ),
+            "gs_num_nodes": ([pp], I64),
+            "gs_stereo_cost_volume": ([P, P, I32, pp, P, P], ctypes.c_int),
+            "gs_build_graph": ([P, pp, P, P, P], ctypes.c_int),
+            "gs_maxflow_solve": ([P, pp, po, P, P, P], ctypes.c_int),
+            "gs_extract_labels": ([P, pp, po, P, P, P, P, P], ctypes.c_int),
+            "gs_energy": ([P, P, pp, P, P], ctypes.c_int),
+            "gs_solve_stats": ([P, P, P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(rc: int, what: str):
+    if rc != GS_OK:
+        raise RuntimeError(f"{what} failed: {STATUS_NAMES.get(rc, rc)}")
+
+
+# ------------------------------------------------------------------ sizes --
+
+def gs_cost_volume_bytes(p: Params) -> int:
+    return lib().gs_cost_volume_bytes(ctypes.byref(p.c()))
+
+
+def gs_graph_bytes(p: Params) -> int:
+    return lib().gs_graph_bytes(ctypes.byref(p.c()))
+
+
+def gs_workspace_bytes(p: Params, o: SolveOpts) -> int:
+    return lib().gs_workspace_bytes(ctypes.byref(p.c()), ctypes.byref(o.c()))
+
+
+def gs_num_nodes(p: Params) -> int:
+    return lib().gs_num_nodes(ctypes.byref(p.c()))
+
+
+# ------------------------------------------------------------------ calls --
+
+def gs_stereo_cost_volume(L: torch.Tensor, R: torch.Tensor, p: Params, cost: torch.Tensor,
+                          stream=None):
+    if L.shape != (p.h, p.w) or R.shape != (p.h, p.w):
+        raise ValueError("L, R must be [h, w]")
+    if cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("cost has the wrong size")
+    rc = lib().gs_stereo_cost_volume(_dev(L, torch.uint8, "L"), _dev(R, torch.uint8, "R"), p.w,
+                                     ctypes.byref(p.c()), _dev(cost, torch.int32, "cost"),
+                                     _stream(stream))
+    _check(rc, "gs_stereo_cost_volume")
+
+
+def gs_build_graph(cost: torch.Tensor, p: Params, graph: torch.Tensor, status: torch.Tensor,
+                   stream=None):
+    if graph.numel() < gs_graph_bytes(p) or cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("graph / cost buffer has the wrong size")
+    rc = lib().gs_build_graph(_dev(cost, torch.int32, "cost"), ctypes.byref(p.c()),
+                              _dev(graph, torch.uint8, "graph"), _dev(status, torch.int32, "status"),
+                              _stream(stream))
+    _check(rc, "gs_build_graph")
+
+
+def gs_maxflow_solve(graph: torch.Tensor, p: Params, o: SolveOpts, workspace: torch.Tensor,
+                     status: torch.Tensor, stream=None):
+    if workspace.numel() < gs_workspace_bytes(p, o):
+        raise ValueError("workspace too small")
+    rc = lib().gs_maxflow_solve(_dev(graph, torch.uint8, "graph"), ctypes.byref(p.c()),
+                                ctypes.byref(o.c()), _dev(workspace, torch.uint8, "workspace"),
+                                _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_maxflow_solve")
+
+
+def gs_extract_labels(graph: torch.Tensor, p: Params, o: SolveOpts, workspace: torch.Tensor,
+                      labels: torch.Tensor, flow: torch.Tensor, status: torch.Tensor, stream=None):
+    if labels.numel() != p.ng * p.h:
+        raise ValueError("labels must hold h * n_g entries")
+    rc = lib().gs_extract_labels(_dev(graph, torch.uint8, "graph"), ctypes.byref(p.c()),
+                                 ctypes.byref(o.c()), _dev(workspace, torch.uint8, "workspace"),
+                                 _dev(labels, torch.int32, "labels"), _dev(flow, torch.int64, "flow"),
+                                 _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_extract_labels")
+
+
+def gs_energy(cost: torch.Tensor, labels: torch.Tensor, p: Params, energy: torch.Tensor,
+              stream=None):
+    rc = lib().gs_energy(_dev(cost, torch.int32, "cost"), _dev(labels, torch.int32, "labels"),
+                         ctypes.byref(p.c()), _dev(energy, torch.int64, "energy"), _stream(stream))
+    _check(rc, "gs_energy")
+
+
+def gs_solve_stats(workspace: torch.Tensor, stream=None) -> dict:
+    out = (ctypes.c_int64 * 8)()
+    rc = lib().gs_solve_stats(_dev(workspace, torch.uint8, "workspace"), out, _stream(stream))
+    _check(rc, "gs_solve_stats")
+    keys = ["relabels", "sweeps", "bfs_passes", "label_passes", "active_at_exit"]
+    return {k: int(out[i]) for i, k in enumerate(keys)}
+
+
+# ---------------------------------------------------------- whole pairs ---
+
+class Buffers:
+    """Device buffers for one problem size (cost volume, graph, workspace, outputs)."""
+
+    def __init__(self, p: Params, o: SolveOpts, device="cuda"):
+        self.p, self.o = p, o
+        self.cost = torch.empty(gs_cost_volume_bytes(p) // 4, dtype=torch.int32, device=device)
+        self.graph = torch.empty(gs_graph_bytes(p), dtype=torch.uint8, device=device)
+        self.work = torch.empty(gs_workspace_bytes(p, o), dtype=torch.uint8, device=device)
+        self.labels = torch.empty((p.h, p.ng), dtype=torch.int32, device=device)
+        self.flow = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def solve_pair(L: torch.Tensor, R: torch.Tensor, p: Params, o: SolveOpts | None = None,
+               buf: Buffers | None = None, stream=None):
+    """All four steps on device images.  Returns (labels, flow, status) device tensors."""
+    o = o or SolveOpts()
+    buf = buf or Buffers(p, o, device=L.device)
+    gs_stereo_cost_volume(L, R, p, buf.cost, stream)
+    gs_build_graph(buf.cost, p, buf.graph, buf.status, stream)
+    gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status, stream)
+    gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status, stream)
+    return buf.labels, buf.flow, buf.status
+
+
+def solve_costs(cost: torch.Tensor, p: Params, o: SolveOpts | None = None,
+                buf: Buffers | None = None, stream=None):
+    """Steps 2-4 from a given cost volume int32 [h, n_g, D]."""
+    o = o or SolveOpts()
+    buf = buf or Buffers(p, o, device=cost.device)
+    c = cost.reshape(-1)
+    gs_build_graph(c, p, buf.graph, buf.status, stream)
+    gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status, stream)
+    gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status, stream)
+    return buf.labels, buf.flow, buf.status

@@ -1,0 +1,88 @@
+"""The C-ABI library builds, loads and exports every entry point the header
+declares; host-side argument checks work without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_01516_gb300 import build
+    build.build()
+    from paper_1803_01516_gb300 import gazecut
+    return gazecut.lib()
+
+
+def _declared():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names += re.findall(r"GS_API\s+[\w\s\*]+?\b(gs_\w+)\s*\(", txt)
+    return names
+
+
+def test_header_declares_the_pipeline():
+    names = _declared()
+    for n in ["gs_stereo_cost_volume", "gs_build_graph", "gs_maxflow_solve", "gs_extract_labels"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_export():
+    from paper_1803_01516_gb300 import gazecut
+    assert sorted(gazecut.EXPORTS) == sorted(_declared())
+
+
+def test_sizes_and_param_validation(lib):
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
+    assert gc.gs_num_nodes(p) == 354 * 288 * 15
+    assert gc.gs_cost_volume_bytes(p) == 4 * 288 * 354 * 16
+    assert gc.gs_graph_bytes(p) >= 36 * 354 * 288 * 15
+    # the paper's cuboid: 372 x 288 sites x 24 depth numbers -> 372*288*23 nodes
+    p2 = gc.Params(w=372 + 46, h=288, D=24, tau=30, lam=14)
+    assert gc.gs_num_nodes(p2) + 2 == 2464130
+    for bad in [gc.Params(w=30, h=4, D=16, tau=1, lam=1),         # n_g <= 0
+                gc.Params(w=64, h=4, D=1, tau=1, lam=1),          # D < 2
+                gc.Params(w=64, h=0, D=4, tau=1, lam=1),
+                gc.Params(w=64, h=4, D=4, tau=1, lam=-1),
+                gc.Params(w=64, h=4, D=4, tau=1, lam=1, dis0=5)]:  # dis0 < 2(D-1)
+        assert gc.gs_graph_bytes(bad) == 0
+        assert gc.gs_num_nodes(bad) == 0
+
+
+def test_null_pointers_rejected_on_host(lib):
+    """Invalid arguments are refused before any launch (no GPU needed)."""
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=64, h=8, D=4, tau=30, lam=2).c()
+    o = gc.SolveOpts().c()
+    assert lib.gs_stereo_cost_volume(None, None, 64, ctypes.byref(p), None, None) == gc.GS_ERR_INVAL
+    assert lib.gs_build_graph(None, ctypes.byref(p), None, None, None) == gc.GS_ERR_INVAL
+    assert lib.gs_maxflow_solve(None, ctypes.byref(p), ctypes.byref(o), None, None, None) == gc.GS_ERR_INVAL
+    assert lib.gs_extract_labels(None, ctypes.byref(p), ctypes.byref(o), None, None, None, None,
+                                 None) == gc.GS_ERR_INVAL
+    assert lib.gs_energy(None, None, ctypes.byref(p), None, None) == gc.GS_ERR_INVAL
+    bad_o = gc.SolveOpts(sweeps_per_relabel=0).c()
+    fake = ctypes.c_void_p(256)
+    assert lib.gs_maxflow_solve(fake, ctypes.byref(p), ctypes.byref(bad_o), fake, fake,
+                                None) == gc.GS_ERR_INVAL
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1803_01516_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
+                assert "gazecut_oracle" not in txt, f

@@ -1,0 +1,165 @@
+"""GPU path vs the CPU oracle, element by element (bit-exact: everything is integer)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01516_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1803_01516_gb300 import build
+    build.build()
+    from paper_1803_01516_gb300 import gazecut
+    return gazecut
+
+
+def _params(gc, wl, vi=1):
+    return gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                     vertical_inhibit=vi)
+
+
+def _solve_costs(gc, C, lam, inhibit, vi, opts=None):
+    h, ng, D = C.shape
+    p = gc.Params(w=ng + 2 * (D - 1), h=h, D=D, tau=0, lam=lam, inhibit=inhibit, vertical_inhibit=vi)
+    opts = opts or gc.SolveOpts()
+    labels, flow, status = gc.solve_costs(torch.from_numpy(np.ascontiguousarray(C)).cuda(), p, opts)
+    torch.cuda.synchronize()
+    return labels.cpu().numpy(), int(flow.item()), int(status.item()), p
+
+
+@pytest.mark.parametrize("which", ["tiny", "main"])
+def test_cost_volume_bit_exact(gc, which):
+    wl = synth.TINY if which == "tiny" else synth.MAIN
+    L, R, _ = synth.make_pair(wl, 0)
+    p = _params(gc, wl)
+    cost = torch.empty(gc.gs_cost_volume_bytes(p) // 4, dtype=torch.int32, device="cuda")
+    gc.gs_stereo_cost_volume(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p, cost)
+    ref = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    assert np.array_equal(cost.cpu().numpy().reshape(ref.shape), ref)
+
+
+@pytest.mark.parametrize("vi", [1, 0])
+def test_tiny_pair_exact(gc, vi):
+    wl = synth.TINY
+    for idx in range(3):
+        L, R, _ = synth.make_pair(wl, idx)
+        p = _params(gc, wl, vi)
+        labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p)
+        torch.cuda.synchronize()
+        C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+        ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
+        assert int(status.item()) == gc.GS_OK
+        assert int(flow.item()) == ref["flow"]
+        assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+
+
+@pytest.mark.parametrize("shape,lam,inh,vi,hi", [
+    ((37, 45, 5), 3, 50, 1, 20),      # ragged in both site dimensions
+    ((19, 70, 9), 2, 1023, 0, 30),    # W spans 3 warps with a ragged tail
+    ((1, 100, 16), 4, 1023, 1, 30),   # one row (chain MRF)
+    ((50, 1, 6), 3, 1023, 1, 30),     # one column
+    ((13, 33, 2), 5, 1023, 1, 30),    # D = 2: one node per site, base flow
+    ((8, 40, 3), 0, 0, 1, 30),        # no interaction: per-site argmin
+    ((21, 64, 7), 1, 3, 1, 40),       # weak inhibit: many jumps of more than 1
+    ((9, 31, 12), 100, 1023, 1, 30),  # strong penalty: nearly constant labeling
+])
+def test_random_costs_exact(gc, shape, lam, inh, vi, hi):
+    rng = np.random.default_rng(sum(shape) * 7 + lam)
+    C = rng.integers(0, hi + 1, size=shape).astype(np.int32)
+    X, flow, status, _ = _solve_costs(gc, C, lam, inh, vi)
+    ref = oracle.solve(C, lam, inh, vi)
+    assert status == gc.GS_OK
+    assert flow == ref["flow"]
+    assert np.array_equal(X, ref["labels"])
+
+
+def test_ties_canonical_labels(gc):
+    """Constant costs: every constant labeling is optimal; the canonical answer
+    is the smallest one (all zeros)."""
+    C = np.full((10, 40, 6), 7, dtype=np.int32)
+    X, flow, status, _ = _solve_costs(gc, C, 3, 1023, 1)
+    assert status == gc.GS_OK and flow == 7 * 400 and (X == 0).all()
+    C = np.random.default_rng(0).integers(0, 3, size=(12, 35, 4)).astype(np.int32)
+    X, flow, status, _ = _solve_costs(gc, C, 1, 2, 1)
+    ref = oracle.solve(C, 1, 2, 1)
+    assert flow == ref["flow"] and np.array_equal(X, ref["labels"])
+    assert (ref["labels"] != ref["labels_max"]).any()
+
+
+@pytest.mark.parametrize("vi", [1, 0])
+def test_main_pair_exact(gc, vi):
+    """The 384x288 pair with 16 depth numbers."""
+    wl = synth.MAIN
+    L, R, _ = synth.make_pair(wl, 0)
+    p = _params(gc, wl, vi)
+    labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p)
+    torch.cuda.synchronize()
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
+    assert int(status.item()) == gc.GS_OK
+    assert int(flow.item()) == ref["flow"]
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+
+
+def test_energy_kernel_matches_oracle(gc):
+    rng = np.random.default_rng(4)
+    C = rng.integers(0, 30, size=(17, 29, 8)).astype(np.int32)
+    X = rng.integers(0, 8, size=(17, 29)).astype(np.int32)
+    p = gc.Params(w=29 + 14, h=17, D=8, tau=0, lam=5, inhibit=99, vertical_inhibit=1)
+    e = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gc.gs_energy(torch.from_numpy(C).cuda().reshape(-1), torch.from_numpy(X).cuda(), p, e)
+    assert int(e.item()) == oracle.energy(C, X, 5, 99, 1)
+
+
+def test_fixed_sweeps_gap_is_nonnegative(gc):
+    wl = synth.TINY
+    L, R, _ = synth.make_pair(wl, 1)
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+    for n in (0, 1, 4, 16):
+        o = gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=n, sweeps_per_relabel=4)
+        X, flow, status, _ = _solve_costs(gc, C, wl.lam, wl.inhibit, 1, o)
+        assert status == gc.GS_OK
+        E = oracle.energy(C, X, wl.lam, wl.inhibit, 1)
+        assert flow <= ref["flow"] <= E          # weak duality on both sides
+
+
+def test_timeout_then_resume(gc):
+    wl = synth.TINY
+    L, R, _ = synth.make_pair(wl, 2)
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+    h, ng, D = C.shape
+    p = gc.Params(w=ng + 2 * (D - 1), h=h, D=D, tau=0, lam=wl.lam, inhibit=wl.inhibit)
+    o = gc.SolveOpts(max_iters=1, sweeps_per_relabel=1)
+    buf = gc.Buffers(p, o)
+    gc.gs_build_graph(torch.from_numpy(C).cuda().reshape(-1), p, buf.graph, buf.status)
+    gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+    assert int(buf.status.item()) == gc.GS_ERR_TIMEOUT
+    buf.status.zero_()
+    o2 = gc.SolveOpts()
+    gc.gs_maxflow_solve(buf.graph, p, o2, buf.work, buf.status)
+    gc.gs_extract_labels(buf.graph, p, o2, buf.work, buf.labels, buf.flow, buf.status)
+    assert int(buf.status.item()) == gc.GS_OK
+    assert int(buf.flow.item()) == ref["flow"]
+    assert np.array_equal(buf.labels.cpu().numpy(), ref["labels"])
+
+
+def test_overflow_and_negative_cost_flagged(gc):
+    p = gc.Params(w=20 + 6, h=4, D=4, tau=0, lam=1, inhibit=10)
+    o = gc.SolveOpts()
+    buf = gc.Buffers(p, o)
+    C = np.zeros((4, 20, 4), dtype=np.int32)
+    C[..., 0] = 1 << 28                      # 80 sites x 2^28 source capacity > 2^30
+    gc.gs_build_graph(torch.from_numpy(C).cuda().reshape(-1), p, buf.graph, buf.status)
+    assert int(buf.status.item()) == gc.GS_ERR_OVERFLOW
+    C[...] = 1
+    C[2, 3, 1] = -1
+    gc.gs_build_graph(torch.from_numpy(C).cuda().reshape(-1), p, buf.graph, buf.status)
+    assert int(buf.status.item()) == gc.GS_ERR_INVAL
