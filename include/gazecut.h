@@ -76,12 +76,25 @@ typedef struct gs_params {
 #define GS_MODE_EXACT        0  /* iterate until no active node can reach the sink */
 #define GS_MODE_FIXED_SWEEPS 1  /* stop after fixed_sweeps local sweeps (approximate cut) */
 
+/* Solver engines.  Both compute the same exact cut; they differ in schedule.
+ *   TILED   one persistent cooperative launch: shared-memory tiles of whole
+ *           depth chains, local push/relabel iterations, tile-local relabel
+ *           passes, grid barriers, no host synchronisation (default)
+ *   SIMPLE  one thread per node, one kernel per sweep / relabel pass, host loop
+ *           (a second, independent schedule kept for cross-checking) */
+#define GS_ENGINE_TILED  0
+#define GS_ENGINE_SIMPLE 1
+
 typedef struct gs_solve_opts {
     int32_t mode;                /* GS_MODE_* */
-    int32_t sweeps_per_relabel;  /* local push-relabel sweeps between global relabels (>= 1) */
+    int32_t sweeps_per_relabel;  /* sweep rounds between global relabels (>= 1) */
     int32_t fixed_sweeps;        /* GS_MODE_FIXED_SWEEPS: total sweeps */
-    int32_t reserved;            /* must be 0 */
+    int32_t engine;              /* GS_ENGINE_* */
     int64_t max_iters;           /* cap on global relabels in exact mode (> 0) */
+    int32_t local_iters;         /* TILED: push/relabel iterations per tile visit (0: 8) */
+    int32_t relabel_passes;      /* TILED: tile passes of an intermediate global relabel
+                                    (0: 8); the relabel that decides termination always
+                                    runs to its fixed point */
 } gs_solve_opts;
 
 /* Derived sizes (0 when the params are invalid). */
@@ -149,8 +162,13 @@ GS_API int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params
 
 /* Diagnostics of the last solve on this workspace: host int64[8] =
  * {global relabels, sweeps, BFS passes, label passes, active nodes at exit,
- *  0, 0, 0}.  Synchronises `stream`. */
+ *  device time of the push-relabel sweeps in ns, device time of the global
+ *  relabels in ns, kernel launches of the solve}.  The two times are measured
+ * with CUDA events on the solve's stream.  Synchronises `stream`. */
 GS_API int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stream);
+
+/* Number of kernels this library has launched in this process so far. */
+GS_API int64_t gs_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -1,7 +1,12 @@
 // Data term (§4.3), energy (§2) and the size queries of the C ABI.
 #include "gs_internal.cuh"
 
+#include <atomic>
+
 namespace gs {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int make_geom(const gs_params *p, Geom *g) {
     if (!p) return GS_ERR_INVAL;
@@ -30,7 +35,7 @@ size_t graph_bytes(const Geom &g) {
 }
 
 size_t work_bytes(const Geom &g) {
-    return 256 + (size_t)round_up(g.N, 64) * sizeof(int32_t);
+    return 256 + (size_t)round_up(g.N * sizeof(int32_t), 256) + tiled_work_extra(g);
 }
 
 State state_view(void *graph, const Geom &g) {
@@ -124,6 +129,8 @@ using namespace gs;
 
 extern "C" {
 
+int64_t gs_kernel_launches(void) { return g_launches.load(); }
+
 int32_t gs_num_sites_w(const gs_params *p) {
     Geom g;
     return make_geom(p, &g) == GS_OK ? g.ng : 0;
@@ -160,6 +167,7 @@ int gs_stereo_cost_volume(const uint8_t *L, const uint8_t *R, int32_t pitch, con
     if (smem > 48 * 1024) return GS_ERR_INVAL;
     k_cost_volume<<<grid, 256, smem, (cudaStream_t)stream>>>(L, R, pitch, g.ng, g.D, p->dis0,
                                                              p->tau, cost);
+    count_launches(1);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -174,6 +182,7 @@ int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, in
     int blocks = (int)std::min<long long>((sites + 255) / 256, 4 * 152);
     k_energy<<<blocks, 256, 0, st>>>(cost, labels, g.ng, g.h, g.D, g.lam, g.h2h, g.h2v,
                                      (unsigned long long *)energy);
+    count_launches(1);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }

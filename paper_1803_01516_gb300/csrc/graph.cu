@@ -34,14 +34,19 @@ __global__ void k_header(GraphHeader *hdr, Geom g, int inhibit, int vinhibit) {
     hdr->max_cost = 0;
 }
 
-// One thread per node.  Chain node j = k-1 of site (W, y):
-//   rc  = C(k) for the data arc n_k -> n_(k+1), k in [1, D-2]
-//   ex  = C(0) at k = 1 (folded source arc) minus C(D-1) at k = D-1 (folded
-//         sink arc); with D = 2 both fold into the same node and min(C0, C1)
-//         flows s -> n -> t directly (base flow)
-//   penalty residuals start at lambda (no flow), inhibit residuals at h2.
+// One thread per node.  Chain node j = k-1 of site (W, y); its incoming data
+// arc carries C(j) (from s when j = 0) and its outgoing one C(j+1) (to t when
+// j = K-1).  The source arcs are folded in as excess and each chain starts
+// with its own largest flow already pushed down it: node j receives
+// F_j = min(C(0..j)) and forwards F_(j+1), so
+//   ex = F_j - F_(j+1)  (j < K-1),   ex = F_(K-1) - C(D-1)  (j = K-1, negative
+//                                     when sink capacity is left: a deficit)
+//   rc = C(j+1) - F_(j+1)  residual of the outgoing data arc.
+// This is a valid preflow (the flow of every chain taken alone, i.e. the cut
+// with no interaction terms); the max-flow routes the rest.  Penalty residuals
+// start at lambda (no flow) and inhibit residuals at h2.
 __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t *status) {
-    unsigned long long base = 0, deficit = 0, src = 0;
+    unsigned long long deficit = 0, src = 0;
     int bad = 0, big = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -54,26 +59,26 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
             continue;
         }
         const int32_t *c = C + ((int64_t)p.y * g.ng + p.W) * g.D;
-        const int k = p.j + 1;
-        int32_t ck = c[k];
-        int32_t rc = (p.j < g.K - 1) ? ck : 0;
-        int64_t e = 0;
-        if (p.j == 0) {
-            const int32_t c0 = c[0];
-            bad |= c0 < 0;
-            big |= c0 > kCapLimit;
-            e += c0;
-            src += (unsigned long long)max(c0, 0);
+        int32_t F = c[0];                 // F_j
+        bad |= F < 0;
+        big |= F > kCapLimit;
+        for (int q = 1; q <= p.j; q++) F = min(F, c[q]);
+        const int32_t cout = c[p.j + 1];  // outgoing arc capacity
+        bad |= cout < 0;
+        big |= cout > kCapLimit;
+        int32_t e, rc;
+        if (p.j < g.K - 1) {
+            const int32_t F1 = min(F, cout);
+            e = F - F1;
+            rc = cout - F1;
+        } else {
+            e = F - cout;
+            rc = 0;
+            deficit += (unsigned long long)max(cout, 0);
         }
-        bad |= ck < 0;
-        big |= ck > kCapLimit;
-        if (p.j == g.K - 1) {
-            e -= c[g.D - 1];
-            if (g.K == 1) base += (unsigned long long)max(min(c[0], c[1]), 0);
-            if (e < 0) deficit += (unsigned long long)(-e);
-        }
+        if (p.j == 0) src += (unsigned long long)max(c[0], 0);
         s.rc[i] = rc;
-        s.ex[i] = (int32_t)e;
+        s.ex[i] = e;
         s.rr[i] = (p.W < g.ng - 1) ? g.lam : 0;
         s.rd[i] = (p.y < g.h - 1) ? g.lam : 0;
         const bool dn = p.j > 0;
@@ -89,7 +94,7 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
     if (__syncthreads_or(big)) {
         if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_OVERFLOW);
     }
-    block_sum_u64(base, &s.hdr->base_flow);
+    // flow value = (total sink capacity) - (sink capacity left at the end)
     block_sum_u64(deficit, &s.hdr->init_deficit);
     block_sum_u64(src, &s.hdr->src_total);
 }
@@ -199,6 +204,7 @@ int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t
     k_header<<<1, 1, 0, st>>>(s.hdr, g, p->inhibit, p->vertical_inhibit);
     k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
     k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
+    count_launches(3);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -214,10 +220,12 @@ int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, v
     const int grid = grid_for(g.N);
     if (o->mode == GS_MODE_EXACT) {
         k_mark_init<<<grid, 256, 0, st>>>(g, s, w.mark);
+        count_launches(1);
         int64_t passes = 0;
         for (;;) {
             GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->changed, 0, sizeof(int32_t), st));
             k_mark_pass<<<grid, 256, 0, st>>>(g, s, w.mark, w.ctrl);
+            count_launches(1);
             int32_t changed = 0;
             GS_CUDA_TRY(cudaMemcpyAsync(&changed, &w.ctrl->changed, sizeof(int32_t),
                                         cudaMemcpyDeviceToHost, st));
@@ -230,15 +238,18 @@ int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, v
                                     cudaMemcpyHostToDevice, st));
         GS_CUDA_TRY(cudaStreamSynchronize(st));
         k_labels<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(g, s, w.mark, 0, labels, status);
+        count_launches(1);
     } else {
         int64_t passes = 0;
         int rc = global_relabel(g, s, w, st, &passes);
         if (rc) return rc;
         k_labels<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(g, s, w.mark, 1, labels, status);
+        count_launches(1);
     }
     GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->deficit_left, 0, sizeof(unsigned long long), st));
     k_deficit<<<grid, 256, 0, st>>>(g, s, &w.ctrl->deficit_left);
     k_flow<<<1, 1, 0, st>>>(s.hdr, w.ctrl, flow);
+    count_launches(3);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }

@@ -56,7 +56,8 @@ struct State {
     int32_t *rc, *rr, *rd, *ri0, *ri1, *ri2, *ri3, *ex, *ht;
 };
 
-// Workspace: control block then one int32 per node.
+// Workspace: control block, one int32 per node (label marks), then the
+// tiled solver's per-node arc masks and per-tile flags.
 struct Ctrl {
     int32_t status;
     int32_t changed;
@@ -64,8 +65,11 @@ struct Ctrl {
     int32_t abort;
     unsigned int bar_count;
     unsigned int bar_gen;
-    int32_t pad[2];
-    long long stats[8];   // relabels, sweeps, bfs passes, label passes, active at exit
+    int32_t converged;
+    int32_t pad;
+    long long bar_red[2][2];
+    long long stats[8];   // relabels, sweeps, bfs passes, label passes, active at exit,
+                          // sweep ns, relabel ns, launches
     unsigned long long deficit_left;
     unsigned long long pad2[3];
 };
@@ -77,6 +81,14 @@ struct Work {
 };
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Process-wide count of kernels this library has launched (diagnostics).
+void count_launches(long long n);
+
+// Tiled persistent solver (tile.cu): extra workspace bytes and the solve.
+size_t tiled_work_extra(const Geom &g);
+int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
+                int32_t *status, cudaStream_t st);
 
 // Validate params and fill the geometry.  Returns GS_OK or GS_ERR_INVAL.
 int make_geom(const gs_params *p, Geom *g);

@@ -112,9 +112,11 @@ static int grid_for(int64_t n) {
 int global_relabel(const Geom &g, const State &s, const Work &w, cudaStream_t st, int64_t *passes) {
     const int grid = grid_for(g.N);
     k_gr_init<<<grid, 256, 0, st>>>(g, s);
+    count_launches(1);
     for (;;) {
         GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->changed, 0, sizeof(int32_t), st));
         k_gr_relax<<<grid, 256, 0, st>>>(g, s, w.ctrl);
+        count_launches(1);
         int32_t changed = 0;
         GS_CUDA_TRY(cudaMemcpyAsync(&changed, &w.ctrl->changed, sizeof(int32_t),
                                     cudaMemcpyDeviceToHost, st));
@@ -125,6 +127,33 @@ int global_relabel(const Geom &g, const State &s, const Work &w, cudaStream_t st
     return GS_OK;
 }
 
+// Event pair that times one phase on the solve's stream.
+struct PhaseTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    double ms = 0;
+    bool pending = false;
+    PhaseTimer() {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~PhaseTimer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    void start(cudaStream_t st) { cudaEventRecord(a, st); }
+    void stop(cudaStream_t st) {
+        cudaEventRecord(b, st);
+        pending = true;
+    }
+    // call after the stream has been synchronised
+    void collect() {
+        if (!pending) return;
+        float t = 0;
+        if (cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms += t;
+        pending = false;
+    }
+};
+
 }  // namespace gs
 
 using namespace gs;
@@ -133,28 +162,37 @@ extern "C" int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_
                                 void *workspace, int32_t *status, void *stream) {
     Geom g;
     if (make_geom(p, &g) != GS_OK || !o || !graph || !workspace || !status) return GS_ERR_INVAL;
-    if (o->sweeps_per_relabel < 1 || o->max_iters < 1 || o->reserved != 0) return GS_ERR_INVAL;
+    if (o->sweeps_per_relabel < 1 || o->max_iters < 1) return GS_ERR_INVAL;
+    if (o->engine != GS_ENGINE_TILED && o->engine != GS_ENGINE_SIMPLE) return GS_ERR_INVAL;
     if (o->mode != GS_MODE_EXACT && o->mode != GS_MODE_FIXED_SWEEPS) return GS_ERR_INVAL;
     if (o->mode == GS_MODE_FIXED_SWEEPS && o->fixed_sweeps < 0) return GS_ERR_INVAL;
     if (((uintptr_t)workspace & 255) != 0) return GS_ERR_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     State s = state_view(graph, g);
     Work w = work_view(workspace, g);
+    if (o->engine == GS_ENGINE_TILED) return tiled_solve(g, s, w, o, status, st);
     const int grid = grid_for(g.N);
     GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
+    PhaseTimer t_sweep, t_relabel;
+    const long long launches0 = gs_kernel_launches();
     int64_t relabels = 0, sweeps = 0, passes = 0, active = 0;
     bool done = false;
     for (int64_t it = 0; !done; it++) {
         if (o->mode == GS_MODE_EXACT && it >= o->max_iters) break;
+        t_relabel.start(st);
         int rc = global_relabel(g, s, w, st, &passes);
         if (rc) return rc;
+        t_relabel.stop(st);
+        t_sweep.collect();
         relabels++;
         GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->active, 0, sizeof(int32_t), st));
         k_count_active<<<grid, 256, 0, st>>>(g, s, w.ctrl);
+        count_launches(1);
         int32_t act = 0;
         GS_CUDA_TRY(cudaMemcpyAsync(&act, &w.ctrl->active, sizeof(int32_t),
                                     cudaMemcpyDeviceToHost, st));
         GS_CUDA_TRY(cudaStreamSynchronize(st));
+        t_relabel.collect();
         active = act;
         if (act == 0) { done = true; break; }
         int n = o->sweeps_per_relabel;
@@ -162,10 +200,18 @@ extern "C" int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_
             n = (int)std::min<int64_t>(n, o->fixed_sweeps - sweeps);
             if (n <= 0) { done = true; break; }
         }
+        t_sweep.start(st);
         for (int k = 0; k < n; k++) k_sweep<<<grid, 256, 0, st>>>(g, s, w.ctrl);
+        count_launches(n);
+        t_sweep.stop(st);
         sweeps += n;
     }
-    long long stats[5] = {relabels, sweeps, passes, 0, active};
+    GS_CUDA_TRY(cudaStreamSynchronize(st));
+    t_sweep.collect();
+    t_relabel.collect();
+    long long stats[8] = {relabels, sweeps, passes, 0, active,
+                          (long long)(t_sweep.ms * 1e6), (long long)(t_relabel.ms * 1e6),
+                          gs_kernel_launches() - launches0};
     GS_CUDA_TRY(cudaMemcpyAsync(w.ctrl->stats, stats, sizeof(stats), cudaMemcpyHostToDevice, st));
     // status: keep an earlier error; else overflow seen by a sweep, else timeout
     int32_t dev = 0;

@@ -21,11 +21,12 @@ LIB_PATH = os.path.join(_HERE, "libgazecut.so")
 GS_OK, GS_ERR_INVAL, GS_ERR_OVERFLOW, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_LABELS = range(6)
 STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "OVERFLOW", 3: "TIMEOUT", 4: "CUDA", 5: "LABELS"}
 GS_MODE_EXACT, GS_MODE_FIXED_SWEEPS = 0, 1
+GS_ENGINE_TILED, GS_ENGINE_SIMPLE = 0, 1
 
 EXPORTS = [
     "gs_num_sites_w", "gs_cost_volume_bytes", "gs_graph_bytes", "gs_workspace_bytes",
     "gs_num_nodes", "gs_stereo_cost_volume", "gs_build_graph", "gs_maxflow_solve",
-    "gs_extract_labels", "gs_energy", "gs_solve_stats",
+    "gs_extract_labels", "gs_energy", "gs_solve_stats", "gs_kernel_launches",
 ]
 
 
@@ -37,8 +38,9 @@ class GsParams(ctypes.Structure):
 
 class GsSolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sweeps_per_relabel", ctypes.c_int32),
-                ("fixed_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("max_iters", ctypes.c_int64)]
+                ("fixed_sweeps", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("max_iters", ctypes.c_int64), ("local_iters", ctypes.c_int32),
+                ("relabel_passes", ctypes.c_int32)]
 
 
 @dataclass
@@ -72,9 +74,13 @@ class SolveOpts:
     sweeps_per_relabel: int = 8
     fixed_sweeps: int = 0
     max_iters: int = 1 << 16
+    engine: int = GS_ENGINE_TILED
+    local_iters: int = 0          # 0: library default
+    relabel_passes: int = 0       # 0: library default
 
     def c(self) -> GsSolveOpts:
-        return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, 0, self.max_iters)
+        return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, self.engine,
+                           self.max_iters, self.local_iters, self.relabel_passes)
 
 
 _lib = None
@@ -103,6 +109,7 @@ def lib():
             "gs_extract_labels": ([P, pp, po, P, P, P, P, P], ctypes.c_int),
             "gs_energy": ([P, P, pp, P, P], ctypes.c_int),
             "gs_solve_stats": ([P, P, P], ctypes.c_int),
+            "gs_kernel_launches": ([], I64),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -206,8 +213,13 @@ def gs_solve_stats(workspace: torch.Tensor, stream=None) -> dict:
     out = (ctypes.c_int64 * 8)()
     rc = lib().gs_solve_stats(_dev(workspace, torch.uint8, "workspace"), out, _stream(stream))
     _check(rc, "gs_solve_stats")
-    keys = ["relabels", "sweeps", "bfs_passes", "label_passes", "active_at_exit"]
+    keys = ["relabels", "sweeps", "bfs_passes", "label_passes", "active_at_exit", "sweep_ns",
+            "relabel_ns", "launches"]
     return {k: int(out[i]) for i, k in enumerate(keys)}
+
+
+def gs_kernel_launches() -> int:
+    return int(lib().gs_kernel_launches())
 
 
 # ---------------------------------------------------------- whole pairs ---

@@ -44,13 +44,18 @@ def test_cost_volume_bit_exact(gc, which):
     assert np.array_equal(cost.cpu().numpy().reshape(ref.shape), ref)
 
 
+ENGINES = [0, 1]   # tiled persistent, simple
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("vi", [1, 0])
-def test_tiny_pair_exact(gc, vi):
+def test_tiny_pair_exact(gc, vi, engine):
     wl = synth.TINY
     for idx in range(3):
         L, R, _ = synth.make_pair(wl, idx)
         p = _params(gc, wl, vi)
-        labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p)
+        o = gc.SolveOpts(engine=engine)
+        labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p, o)
         torch.cuda.synchronize()
         C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
         ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
@@ -68,11 +73,15 @@ def test_tiny_pair_exact(gc, vi):
     ((8, 40, 3), 0, 0, 1, 30),        # no interaction: per-site argmin
     ((21, 64, 7), 1, 3, 1, 40),       # weak inhibit: many jumps of more than 1
     ((9, 31, 12), 100, 1023, 1, 30),  # strong penalty: nearly constant labeling
+    ((7, 45, 64), 3, 1023, 1, 30),    # long chains (D = 64)
+    ((3, 21, 128), 2, 1023, 0, 40),   # D = 128, narrow tiles
+    ((11, 97, 16), 10, 1023, 1, 30),  # several tiles in both directions
 ])
-def test_random_costs_exact(gc, shape, lam, inh, vi, hi):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_random_costs_exact(gc, shape, lam, inh, vi, hi, engine):
     rng = np.random.default_rng(sum(shape) * 7 + lam)
     C = rng.integers(0, hi + 1, size=shape).astype(np.int32)
-    X, flow, status, _ = _solve_costs(gc, C, lam, inh, vi)
+    X, flow, status, _ = _solve_costs(gc, C, lam, inh, vi, gc.SolveOpts(engine=engine))
     ref = oracle.solve(C, lam, inh, vi)
     assert status == gc.GS_OK
     assert flow == ref["flow"]
@@ -92,13 +101,15 @@ def test_ties_canonical_labels(gc):
     assert (ref["labels"] != ref["labels_max"]).any()
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("vi", [1, 0])
-def test_main_pair_exact(gc, vi):
+def test_main_pair_exact(gc, vi, engine):
     """The 384x288 pair with 16 depth numbers."""
     wl = synth.MAIN
     L, R, _ = synth.make_pair(wl, 0)
     p = _params(gc, wl, vi)
-    labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p)
+    o = gc.SolveOpts(engine=engine)
+    labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p, o)
     torch.cuda.synchronize()
     C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
     ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
@@ -117,33 +128,36 @@ def test_energy_kernel_matches_oracle(gc):
     assert int(e.item()) == oracle.energy(C, X, 5, 99, 1)
 
 
-def test_fixed_sweeps_gap_is_nonnegative(gc):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_fixed_sweeps_gap_is_nonnegative(gc, engine):
     wl = synth.TINY
     L, R, _ = synth.make_pair(wl, 1)
     C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
     ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
     for n in (0, 1, 4, 16):
-        o = gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=n, sweeps_per_relabel=4)
+        o = gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=n, sweeps_per_relabel=4,
+                         engine=engine)
         X, flow, status, _ = _solve_costs(gc, C, wl.lam, wl.inhibit, 1, o)
         assert status == gc.GS_OK
         E = oracle.energy(C, X, wl.lam, wl.inhibit, 1)
         assert flow <= ref["flow"] <= E          # weak duality on both sides
 
 
-def test_timeout_then_resume(gc):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_timeout_then_resume(gc, engine):
     wl = synth.TINY
     L, R, _ = synth.make_pair(wl, 2)
     C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
     ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
     h, ng, D = C.shape
     p = gc.Params(w=ng + 2 * (D - 1), h=h, D=D, tau=0, lam=wl.lam, inhibit=wl.inhibit)
-    o = gc.SolveOpts(max_iters=1, sweeps_per_relabel=1)
+    o = gc.SolveOpts(max_iters=1, sweeps_per_relabel=1, engine=engine)
     buf = gc.Buffers(p, o)
     gc.gs_build_graph(torch.from_numpy(C).cuda().reshape(-1), p, buf.graph, buf.status)
     gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
     assert int(buf.status.item()) == gc.GS_ERR_TIMEOUT
     buf.status.zero_()
-    o2 = gc.SolveOpts()
+    o2 = gc.SolveOpts(engine=engine)
     gc.gs_maxflow_solve(buf.graph, p, o2, buf.work, buf.status)
     gc.gs_extract_labels(buf.graph, p, o2, buf.work, buf.labels, buf.flow, buf.status)
     assert int(buf.status.item()) == gc.GS_OK
