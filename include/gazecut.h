@@ -60,6 +60,7 @@ extern "C" {
 #define GS_ERR_TIMEOUT   3   /* max_iters reached before the cut was exact; state stays valid */
 #define GS_ERR_CUDA      4   /* a CUDA launch or copy failed */
 #define GS_ERR_LABELS    5   /* the cut was not one depth number per gaze line (internal check) */
+#define GS_ERR_TOO_LARGE 6   /* the problem needs more scratch than gs_noalloc_scratch_bytes() */
 
 /* Problem description.  tau is used by the cost-volume call only. */
 typedef struct gs_params {
@@ -169,6 +170,32 @@ GS_API int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stre
 
 /* Number of kernels this library has launched in this process so far. */
 GS_API int64_t gs_kernel_launches(void);
+
+/*
+ * gs_maxflow_solve without a workspace argument (the paper has no
+ * counterpart: this is an interface for callers of the library).
+ *
+ * For callers that cannot allocate device memory when they solve, e.g. a
+ * real-time loop that reserves all its memory at start-up, or a plug-in whose
+ * host application owns the device allocator.  The solver's scratch lives in
+ * a library-owned static device array of gs_noalloc_scratch_bytes() bytes
+ * (16 MiB) that every GPU loading this library holds until the process exits.
+ * The call itself allocates nothing.
+ *
+ * graph, p, o, status, stream: as for gs_maxflow_solve; o->engine must be
+ * GS_ENGINE_TILED.  Returns GS_ERR_TOO_LARGE, before any device work, when the
+ * problem needs more scratch than the array holds (about 6.5 bytes per graph
+ * node: 384x288 with 16 depth numbers fits, 1920x1080 with 128 does not).
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array (it keeps the last call's contents; the solve clears
+ * what must start at zero), so calls that overlap on the GPU race: issue them
+ * on one stream or serialise them.  gs_extract_labels still takes its own
+ * workspace.
+ */
+GS_API size_t gs_noalloc_scratch_bytes(void);
+GS_API int gs_maxflow_solve_noalloc(void *graph, const gs_params *p, const gs_solve_opts *o,
+                                    int32_t *status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -18,8 +18,10 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgazecut.so")
 
-GS_OK, GS_ERR_INVAL, GS_ERR_OVERFLOW, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_LABELS = range(6)
-STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "OVERFLOW", 3: "TIMEOUT", 4: "CUDA", 5: "LABELS"}
+GS_OK, GS_ERR_INVAL, GS_ERR_OVERFLOW, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_LABELS, \
+    GS_ERR_TOO_LARGE = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "OVERFLOW", 3: "TIMEOUT", 4: "CUDA", 5: "LABELS",
+                6: "TOO_LARGE"}
 GS_MODE_EXACT, GS_MODE_FIXED_SWEEPS = 0, 1
 GS_ENGINE_TILED, GS_ENGINE_SIMPLE = 0, 1
 
@@ -27,6 +29,7 @@ EXPORTS = [
     "gs_num_sites_w", "gs_cost_volume_bytes", "gs_graph_bytes", "gs_workspace_bytes",
     "gs_num_nodes", "gs_stereo_cost_volume", "gs_build_graph", "gs_maxflow_solve",
     "gs_extract_labels", "gs_energy", "gs_solve_stats", "gs_kernel_launches",
+    "gs_noalloc_scratch_bytes", "gs_maxflow_solve_noalloc",
 ]
 
 
@@ -110,6 +113,8 @@ def lib():
             "gs_energy": ([P, P, pp, P, P], ctypes.c_int),
             "gs_solve_stats": ([P, P, P], ctypes.c_int),
             "gs_kernel_launches": ([], I64),
+            "gs_noalloc_scratch_bytes": ([], SZ),
+            "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -220,6 +225,19 @@ def gs_solve_stats(workspace: torch.Tensor, stream=None) -> dict:
 
 def gs_kernel_launches() -> int:
     return int(lib().gs_kernel_launches())
+
+
+def gs_noalloc_scratch_bytes() -> int:
+    return int(lib().gs_noalloc_scratch_bytes())
+
+
+def gs_maxflow_solve_noalloc(graph: torch.Tensor, p: Params, o: SolveOpts, status: torch.Tensor,
+                             stream=None) -> int:
+    """Solve with the library's static scratch (no workspace).  Returns the
+    host status (GS_ERR_TOO_LARGE when the problem does not fit)."""
+    return lib().gs_maxflow_solve_noalloc(_dev(graph, torch.uint8, "graph"), ctypes.byref(p.c()),
+                                          ctypes.byref(o.c()), _dev(status, torch.int32, "status"),
+                                          _stream(stream))
 
 
 # ---------------------------------------------------------- whole pairs ---

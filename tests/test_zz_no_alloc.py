@@ -1,0 +1,62 @@
+"""gs_maxflow_solve_noalloc: the solve for callers that cannot allocate device
+memory at solve time (scratch in the library's static device array).
+
+Its results must equal those of gs_maxflow_solve with a caller workspace, on
+consecutive calls that reuse the static scratch.  This file is collected last
+so that a run stopping at the first failure has run every other test first.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1803_01516_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_1803_01516_gb300 import build
+    build.build()
+    from paper_1803_01516_gb300 import gazecut
+    return gazecut
+
+
+def test_too_large_is_rejected_before_any_device_work(gc):
+    """A problem needing more scratch than the static array holds is refused
+    on the host (no GPU needed for this check)."""
+    p = gc.Params(w=1920, h=1080, D=128, tau=40, lam=12)
+    o = gc.SolveOpts()
+    fake = ctypes.c_void_p(256)
+    rc = gc.lib().gs_maxflow_solve_noalloc(fake, ctypes.byref(p.c()), ctypes.byref(o.c()), fake,
+                                           None)
+    assert rc == gc.GS_ERR_TOO_LARGE
+    assert gc.gs_noalloc_scratch_bytes() == 16 << 20
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_workspace_solve_on_consecutive_calls(gc):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    dev = torch.device("cuda")
+    for wl, idx in [(synth.MAIN, 0), (synth.MAIN, 1), (synth.TINY, 2)]:
+        L, R, _ = synth.make_pair(wl, idx)
+        p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit)
+        o = gc.SolveOpts()
+        Ld, Rd = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
+        # the existing entry point with a caller workspace
+        ref = gc.Buffers(p, o, device=dev)
+        gc.solve_pair(Ld, Rd, p, o, ref)
+        # the same problem through the no-allocation entry point
+        buf = gc.Buffers(p, o, device=dev)
+        gc.gs_stereo_cost_volume(Ld, Rd, p, buf.cost)
+        gc.gs_build_graph(buf.cost, p, buf.graph, buf.status)
+        rc = gc.gs_maxflow_solve_noalloc(buf.graph, p, o, buf.status)
+        assert rc == gc.GS_OK
+        gc.gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status)
+        torch.cuda.synchronize()
+        assert int(ref.status.item()) == gc.GS_OK
+        assert int(buf.status.item()) == gc.GS_OK
+        assert int(buf.flow.item()) == int(ref.flow.item())
+        assert np.array_equal(buf.labels.cpu().numpy(), ref.labels.cpu().numpy())
