@@ -217,6 +217,7 @@ int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, v
     cudaStream_t st = (cudaStream_t)stream;
     State s = state_view(graph, g);
     Work w = work_view(workspace, g);
+    if (o->engine == GS_ENGINE_TILED) return tiled_extract(g, s, w, o, labels, flow, status, st);
     const int grid = grid_for(g.N);
     if (o->mode == GS_MODE_EXACT) {
         k_mark_init<<<grid, 256, 0, st>>>(g, s, w.mark);

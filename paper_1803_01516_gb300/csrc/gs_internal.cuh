@@ -89,6 +89,8 @@ void count_launches(long long n);
 size_t tiled_work_extra(const Geom &g);
 int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
                 int32_t *status, cudaStream_t st);
+int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
+                  int32_t *labels, int64_t *flow, int32_t *status, cudaStream_t st);
 
 // Validate params and fill the geometry.  Returns GS_OK or GS_ERR_INVAL.
 int make_geom(const gs_params *p, Geom *g);

@@ -53,6 +53,9 @@ struct SolveArgs {
     int32_t *tile_dirty; // [2][T] tiles whose halo heights changed in the last relabel pass
     int32_t *tile_cnt;   // [T] active nodes per tile after its last relabel pass
     void *log;           // diagnostics: per-relabel counters (label-mark buffer)
+    int32_t *hgt;        // distances the relabel passes compute (state heights, or marks)
+    int dir;             // 0: distance to sink capacity over out-arcs (heights);
+                         // 1: distance from positive excess over in-arcs (reachability)
     Ctrl *ctrl;
     int mode, sweeps_per_relabel, local_iters, relabel_passes;
     long long fixed_sweeps, max_iters;
@@ -283,7 +286,7 @@ __device__ __forceinline__ TileOrigin tile_origin(const TileGeom &t, int tile) {
 // at y0-1; ri2 at y0+TH).  Positions outside the grid get height kInfH and
 // zero residuals.
 __device__ void load_halo(const SolveArgs &a, const TileSmem &m, const TileOrigin &o,
-                          bool with_residuals) {
+                          bool with_residuals, const int32_t *hsrc) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const State &s = a.s;
@@ -297,7 +300,7 @@ __device__ void load_halo(const SolveArgs &a, const TileSmem &m, const TileOrigi
         const int pi = pidx(t, yl, j, wl);
         const bool in = W >= 0 && W < g.ng && y < g.h;
         const int64_t gi = ((int64_t)y * g.K + j) * g.P + W;
-        m.ht[pi] = in ? ld(&s.ht[gi]) : kInfH;
+        m.ht[pi] = in ? ld(&hsrc[gi]) : kInfH;
         if (with_residuals) {
             if (side == 0) {
                 m.rr[pi] = in ? ld(&s.rr[gi]) : 0;
@@ -317,7 +320,7 @@ __device__ void load_halo(const SolveArgs &a, const TileSmem &m, const TileOrigi
         const int pi = pidx(t, yl, j, wl);
         const bool in = y >= 0 && y < g.h && W < g.ng;
         const int64_t gi = ((int64_t)y * g.K + j) * g.P + W;
-        m.ht[pi] = in ? ld(&s.ht[gi]) : kInfH;
+        m.ht[pi] = in ? ld(&hsrc[gi]) : kInfH;
         if (with_residuals) {
             if (side == 0) {
                 m.rd[pi] = in ? ld(&s.rd[gi]) : 0;
@@ -402,7 +405,7 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
     const TileGeom &t = a.t;
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
-    load_halo(a, m, o, true);
+    load_halo(a, m, o, true, a.hgt);
     int pi[NPT];
     unsigned mk[NPT];
     int64_t gi[NPT];
@@ -431,8 +434,12 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
         m.ri2[p] = ld(&s.ri2[i]);
         m.ri3[p] = ld(&s.ri3[i]);
         const int32_t e = ld(&s.ex[i]);
-        m.ht[p] = e < 0 ? 0 : kInfH;
-        mk[k] = e > 0 ? 0x8000u : 0u;
+        if (a.dir == 0) {
+            m.ht[p] = e < 0 ? 0 : kInfH;
+            mk[k] = e > 0 ? 0x8000u : 0u;
+        } else {
+            m.ht[p] = e > 0 ? 0 : kInfH;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -442,9 +449,22 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
         const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
         const unsigned ex = arc_exists(g, o.y0 + yl, j, o.W0 + wl);
 #pragma unroll
-        for (int q = 0; q < kSlots; q++)
-            if ((ex >> q) & 1u)
-                if (smem_residual(m, t, g, pi[k], q) > 0) mk[k] |= 1u << q;
+        for (int q = 0; q < kSlots; q++) {
+            if (!((ex >> q) & 1u)) continue;
+            bool res;
+            if (a.dir == 0) {
+                res = smem_residual(m, t, g, pi[k], q) > 0;          // arc u -> head
+            } else if (q == 0) {
+                res = true;                                           // head j+1 -> u: infinite
+            } else if (q == 1) {
+                res = m.rc[pi[k] - t.SJ] > 0;                         // head j-1 -> u: data arc
+            } else {
+                const int32_t cap = q < 6 ? g.lam2 : (q == 8 || q == 9 || q == 12 || q == 13) ? g.h2v
+                                                                                             : g.h2h;
+                res = cap - smem_residual(m, t, g, pi[k], q) > 0;     // head -> u: pair reverse
+            }
+            if (res) mk[k] |= 1u << q;
+        }
         __stcg(&a.amask[gi[k]], (uint16_t)mk[k]);
     }
     // halo heights are not known yet in this pass: treat as infinite
@@ -465,7 +485,7 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
     for (int k = 0; k < NPT; k++) {
         if (pi[k] < 0) continue;
         const int32_t h = m.ht[pi[k]];
-        __stcg(&s.ht[gi[k]], h);
+        __stcg(&a.hgt[gi[k]], h);
         act += (mk[k] & 0x8000u) && h < kInfH;
     }
     const long long tot = block_sum(act);
@@ -483,7 +503,7 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
     const TileGeom &t = a.t;
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
-    load_halo(a, m, o, false);
+    load_halo(a, m, o, false, a.hgt);
     int pi[NPT];
     unsigned mk[NPT];
     int64_t gi[NPT];
@@ -507,7 +527,7 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
         pi[k] = p;
         gi[k] = i;
         mk[k] = ld(&a.amask[i]);
-        h0[k] = ld(&s.ht[i]);
+        h0[k] = ld(&a.hgt[i]);
         m.ht[p] = h0[k];
     }
     __shared__ int s_sides;
@@ -521,7 +541,7 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
         if (pi[k] < 0) continue;
         const int32_t h = m.ht[pi[k]];
         if (h != h0[k]) {
-            __stcg(&s.ht[gi[k]], h);
+            __stcg(&a.hgt[gi[k]], h);
             const int n = threadIdx.x + k * blockDim.x;
             const int wl = n % t.TW, yl = (n / t.TW) / g.K;
             sides |= (wl == 0 ? 1u : 0u) | (wl == t.TW - 1 ? 2u : 0u) | (yl == 0 ? 4u : 0u) |
@@ -556,7 +576,7 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
     int32_t *act_next = a.tile_act + ((round + 1) & 1) * t.T;
-    load_halo(a, m, o, true);
+    load_halo(a, m, o, true, s.ht);
     int pi[NPT];
     int64_t gi[NPT];
     unsigned ex_bits[NPT];
@@ -845,6 +865,85 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
     }
 }
 
+// ------------------------------------------------------------ labels ---
+
+// Reads the cut of the solved state back as labels, in one cooperative launch.
+// Exact mode: S_min = nodes reachable from positive excess over residual
+// arcs (dir 1, sources = excess nodes); a site's label is the number of its
+// chain nodes in S_min.  Fixed-sweep mode: the source side is the set of nodes
+// that cannot reach sink capacity (dir 0, exact distances, label = number of
+// chain nodes at infinite distance).  Both searches run to their fixed point.
+// The flow value is the sink capacity used: initial minus remaining deficit.
+template <int NPT>
+__global__ void __launch_bounds__(kTileThreads, 1)
+    k_extract_tiled(SolveArgs a, int32_t *labels, int64_t *flow, int32_t *status) {
+    extern __shared__ int32_t smem[];
+    const TileSmem m = tile_smem(smem, a.t.PN);
+    Ctrl *ctrl = a.ctrl;
+    const Geom &g = a.g;
+    const TileGeom &t = a.t;
+    const int T = t.T;
+    __shared__ int s_work;
+    long long passes = 1;
+    for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+        relabel_init_tile<NPT>(a, m, tile);
+        if (threadIdx.x == 0) {
+            __stcg(&a.tile_dirty[tile], 0);
+            __stcg(&a.tile_dirty[T + tile], 0);
+        }
+    }
+    grid_sync_sum(ctrl, 0);
+    for (int pass = 1; !aborted(ctrl); pass++) {
+        int changed = 0;
+        int32_t *dcur = a.tile_dirty + (pass & 1) * T;
+        int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
+        for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+            if (pass > 1) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_work = ld(&dcur[tile]);
+                __syncthreads();
+                if (!s_work) continue;
+                if (threadIdx.x == 0) __stcg(&dcur[tile], 0);
+            }
+            relabel_pass_tile<NPT>(a, m, tile, changed, dnext);
+        }
+        const Sum2 r = grid_sync_sum2(ctrl, 0, threadIdx.x == 0 ? changed : 0);
+        passes++;
+        if (r.b == 0) break;
+    }
+    // labels of the tiles' sites and the sink capacity left
+    unsigned long long deficit = 0;
+    int bad = 0;
+    for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+        const TileOrigin o = tile_origin(t, tile);
+        for (int sidx = threadIdx.x; sidx < t.TW * t.TH; sidx += blockDim.x) {
+            const int wl = sidx % t.TW, yl = sidx / t.TW;
+            const int W = o.W0 + wl, y = o.y0 + yl;
+            if (W >= g.ng || y >= g.h) continue;
+            int64_t i = (int64_t)y * g.SY + W;
+            int lab = 0, prev = 1;
+            for (int j = 0; j < g.K; j++, i += g.P) {
+                const int32_t h = ld(&a.hgt[i]);
+                const int in = a.dir == 1 ? (h < kInfH) : (h >= kInfH);
+                bad |= in && !prev;
+                lab += in;
+                prev = in;
+                const int32_t e = ld(&a.s.ex[i]);
+                if (e < 0) deficit += (unsigned long long)(-(int64_t)e);
+            }
+            labels[(int64_t)y * g.ng + W] = lab;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_LABELS);
+    const long long tot = block_sum((long long)deficit);
+    const long long all = grid_sync_sum(ctrl, threadIdx.x == 0 ? tot : 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *flow = (int64_t)a.s.hdr->init_deficit - all;
+        ctrl->stats[3] = passes;
+        if (aborted(ctrl)) atomicCAS(status, GS_OK, GS_ERR_TIMEOUT);
+    }
+}
+
 // copy the solve's device status into the caller's word unless it holds an error
 __global__ void k_publish_status(Ctrl *ctrl, int32_t *status, int launches) {
     if (*status == GS_OK && ctrl->status != GS_OK) *status = ctrl->status;
@@ -896,13 +995,10 @@ size_t tiled_work_extra(const Geom &g) {
     return round_up(g.N * sizeof(uint16_t), 256) + round_up(5 * (int64_t)t.T * sizeof(int32_t), 256);
 }
 
-int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
-                int32_t *status, cudaStream_t st) {
-    SolveArgs a;
+static int setup_args(const Geom &g, const State &s, const Work &w, SolveArgs &a, int &npt,
+                      size_t &smem) {
     a.g = g;
     a.s = s;
-    int npt;
-    size_t smem;
     if (!pick_tile(g, a.t, npt, smem)) return GS_ERR_INVAL;
     char *extra = (char *)w.mark + round_up(g.N * sizeof(int32_t), 256);
     a.amask = (uint16_t *)extra;
@@ -911,13 +1007,12 @@ int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opt
     a.tile_cnt = a.tile_act + 4 * a.t.T;
     a.log = w.mark;
     a.ctrl = w.ctrl;
-    a.mode = o->mode;
-    a.sweeps_per_relabel = o->sweeps_per_relabel;
-    a.local_iters = o->local_iters > 0 ? o->local_iters : 8;
-    a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 4;
-    a.fixed_sweeps = o->fixed_sweeps;
-    a.max_iters = o->max_iters;
-    void (*kern)(SolveArgs) = npt == 4 ? k_solve_tiled<4> : k_solve_tiled<8>;
+    return GS_OK;
+}
+
+// Cooperative launch of kern with the whole grid resident.
+template <class... Args>
+static int launch_coop(void (*kern)(Args...), size_t smem, int T, cudaStream_t st, void **args) {
     int dev = 0;
     GS_CUDA_TRY(cudaGetDevice(&dev));
     int sms = 0, coop = 0;
@@ -928,13 +1023,53 @@ int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opt
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem));
     if (per_sm < 1) return GS_ERR_INVAL;
-    const int grid = std::min(per_sm * sms, a.t.T);
-    GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
-    void *args[] = {&a};
+    const int grid = std::min(per_sm * sms, T);
     GS_CUDA_TRY(cudaLaunchCooperativeKernel((void *)kern, grid, kTileThreads, args, smem, st));
     count_launches(1);
+    return GS_OK;
+}
+
+int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
+                int32_t *status, cudaStream_t st) {
+    SolveArgs a;
+    int npt;
+    size_t smem;
+    int rc = setup_args(g, s, w, a, npt, smem);
+    if (rc) return rc;
+    a.hgt = s.ht;
+    a.dir = 0;
+    a.mode = o->mode;
+    a.sweeps_per_relabel = o->sweeps_per_relabel;
+    a.local_iters = o->local_iters > 0 ? o->local_iters : 8;
+    a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 4;
+    a.fixed_sweeps = o->fixed_sweeps;
+    a.max_iters = o->max_iters;
+    GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
+    void *args[] = {&a};
+    rc = npt == 4 ? launch_coop(k_solve_tiled<4>, smem, a.t.T, st, args)
+                  : launch_coop(k_solve_tiled<8>, smem, a.t.T, st, args);
+    if (rc) return rc;
     k_publish_status<<<1, 1, 0, st>>>(w.ctrl, status, 2);
     count_launches(1);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
+                  int32_t *labels, int64_t *flow, int32_t *status, cudaStream_t st) {
+    SolveArgs a;
+    int npt;
+    size_t smem;
+    int rc = setup_args(g, s, w, a, npt, smem);
+    if (rc) return rc;
+    a.hgt = w.mark;
+    a.dir = o->mode == GS_MODE_EXACT ? 1 : 0;
+    // control words only: keep the solve's statistics, reset the barrier
+    GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, offsetof(Ctrl, stats), st));
+    void *args[] = {&a, &labels, &flow, &status};
+    rc = npt == 4 ? launch_coop(k_extract_tiled<4>, smem, a.t.T, st, args)
+                  : launch_coop(k_extract_tiled<8>, smem, a.t.T, st, args);
+    if (rc) return rc;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
