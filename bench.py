@@ -9,11 +9,13 @@ the timed events.
 Extra keys on the JSON line:
   e2e           the same metric through the public API from pinned host images
                 to host labels (H2D + four C-ABI calls + D2H inside the timing)
-  roofline      the push-relabel sweep kernel: algorithmic bytes (72 B per node
-                per sweep) / its average launch time, measured with CUDA events
-                on the solve's stream during the timed steps, against the
-                measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle (Boykov-Kolmogorov) on a bounded sample
+  roofline      the persistent solve kernel (the dominant one): algorithmic
+                bytes (72 B per node of every tile a sweep round visits, 40 B
+                per node of every tile a relabel pass visits) / its launch
+                time, measured with CUDA events on the solve's stream during
+                the timed steps, against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle (Boykov-Kolmogorov) on the bench's distinct pairs,
+                whose results also check the timed GPU results (parity_vs_oracle)
   clocks        SM clocks and throttle reasons sampled during the timed steps
 
 --impl reference times the CPU oracle on the same workload (the reference arm).
@@ -40,6 +42,7 @@ from paper_1803_01516_gb300 import synth  # noqa: E402
 METRIC = "ms/pair exact min-cut at 384x288x16"
 UNIT = "ms/pair"
 BYTES_PER_NODE_SWEEP = 72      # 9 int32 words read and written once per node per sweep
+BYTES_PER_NODE_BFS = 40        # 9 words read, the height written, per node per BFS level
 N_PAIRS = 4                    # distinct seeded pairs, cycled over the steps
 
 
@@ -54,6 +57,26 @@ def _config(wl, extra=None):
     if extra:
         c.update(extra)
     return c
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the solve kernel from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_solve_tiled_main-384x288x16.md")
+    src = os.path.join(ROOT, "paper_1803_01516_gb300", "csrc", "tile.cu")
+    try:
+        kv = {}
+        for line in open(prof):
+            if ":" in line and not line.startswith(("|", " ", "#")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("kernel_source_sha256_16") != sha:
+            return None
+        return int(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def _peaks():
@@ -122,26 +145,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_baseline(wl, budget_s=20.0):
-    """Time the CPU oracle (cost volume + Boykov-Kolmogorov) on whole pairs
-    until about budget_s seconds of CPU work have been spent."""
+def _cpu_baseline(wl, pairs):
+    """The CPU oracle (cost volume + Boykov-Kolmogorov, single-threaded) on the
+    bench's distinct pairs; returns the timing line and the oracle solutions."""
     import oracle
     oracle.build()
-    times = []
-    t_all = time.perf_counter()
-    i = 0
-    while True:
-        L, R, _ = synth.make_pair(wl, i % N_PAIRS)
+    times, refs = [], []
+    for L, R, _ in pairs:
         t0 = time.perf_counter()
         C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
-        oracle.solve(C, wl.lam, wl.inhibit, 1, "bk")
+        refs.append(oracle.solve(C, wl.lam, wl.inhibit, 1, "bk"))
         times.append(time.perf_counter() - t0)
-        i += 1
-        if time.perf_counter() - t_all > budget_s or i >= 16:
-            break
-    return {"value": 1e3 * float(np.mean(times)), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} whole {wl.w}x{wl.h}x{wl.D} pairs, single-threaded "
-                      f"Boykov-Kolmogorov + cost volume, mean ms/pair"}
+    cpu = {"value": 1e3 * float(np.mean(times)), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"the {len(pairs)} distinct {wl.w}x{wl.h}x{wl.D} pairs of the timed steps, "
+                     "whole pairs, single-threaded Boykov-Kolmogorov + cost volume, mean ms/pair"}
+    return cpu, refs
 
 
 def _dist_env():
@@ -201,7 +219,8 @@ def run(args):
     wl = _workload()
     p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
                   vertical_inhibit=1)
-    o = gc.SolveOpts(sweeps_per_relabel=args.sweeps_per_relabel)
+    o = gc.SolveOpts(sweeps_per_relabel=args.sweeps_per_relabel, local_iters=args.local_iters,
+                     relabel_passes=args.relabel_passes)
     # each rank solves its own pairs (replicas)
     pairs = [synth.make_pair(wl, rank * N_PAIRS + i) for i in range(N_PAIRS)]
     Ld = [torch.from_numpy(L).to(dev) for L, _, _ in pairs]
@@ -210,8 +229,24 @@ def run(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(i):
-        gc.solve_pair(Ld[i % N_PAIRS], Rd[i % N_PAIRS], p, o, buf)
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def step(i, evs=None):
+        """One pair: cost volume + graph build | max-flow solve | label extraction."""
+        k = i % N_PAIRS
+        if evs:
+            evs[0].record(stream)
+        gc.gs_stereo_cost_volume(Ld[k], Rd[k], p, buf.cost)
+        gc.gs_build_graph(buf.cost, p, buf.graph, buf.status)
+        if evs:
+            evs[1].record(stream)
+        gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+        if evs:
+            evs[2].record(stream)
+        gc.gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status)
+        if evs:
+            evs[3].record(stream)
 
     for i in range(args.warmup):
         step(i)
@@ -226,31 +261,28 @@ def run(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    evs = [[ev() for _ in range(4)] for _ in range(args.steps)]
     launches0 = gc.gs_kernel_launches()
-    sweep_ns = relabel_ns = sweeps = relabels = passes = 0
+    stats = []
+    bad_status = 0
     for i in range(args.steps):
-        flush.fill_(i & 0xff)
-        ev[i][0].record(stream)
-        step(i)
-        ev[i][1].record(stream)
-        st = gc.gs_solve_stats(buf.work)
-        sweep_ns += st["sweep_ns"]
-        relabel_ns += st["relabel_ns"]
-        sweeps += st["sweeps"]
-        relabels += st["relabels"]
-        passes += st["bfs_passes"]
+        flush.fill_(i & 0xff)                       # L2 flush, outside the timed events
+        step(i, evs[i])
+        stats.append(gc.gs_solve_stats(buf.work))   # synchronises, after the last event
+        bad_status |= int(buf.status.item()) != gc.GS_OK
     torch.cuda.synchronize(dev)
     launches = gc.gs_kernel_launches() - launches0
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t_wall
-    ms_steps = [a.elapsed_time(b) for a, b in ev]
-    my_ms = float(sum(ms_steps))
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    solve_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    extract_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    my_ms = float(sum(step_ms))
     clk = clocks.stop() if rank == 0 else None
-    if int(buf.status.item()) != gc.GS_OK:
-        raise RuntimeError(f"solve status {buf.status.item()}")
+    if bad_status:
+        raise RuntimeError("a timed solve did not end with GS_OK")
     if dist:
         t = torch.tensor([my_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -272,7 +304,7 @@ def run(args):
         e2e_ms = []
         for i in range(args.steps):
             flush.fill_(i & 0xff)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a, b = ev(), ev()
             a.record(stream)
             Lbuf.copy_(Lh[i % N_PAIRS], non_blocking=True)
             Rbuf.copy_(Rh[i % N_PAIRS], non_blocking=True)
@@ -291,31 +323,56 @@ def run(args):
             dist.destroy_process_group()
         return 0
 
+    # ----- roofline of the dominant kernel (the persistent solve) -----
     peak, peak_kind = _peaks()
     nodes = gc.gs_num_nodes(p)
-    bytes_per_sweep = BYTES_PER_NODE_SWEEP * nodes
-    sweep_launch_s = (sweep_ns * 1e-9) / max(sweeps, 1)
-    achieved = bytes_per_sweep / sweep_launch_s / 1e9 if sweeps else 0.0
-    cpu = None if args.no_cpu_baseline or world > 1 else _cpu_baseline(wl)
+    ti = gc.gs_tile_info(p)
+    nodes_per_tile = nodes / ti["tiles"]
+    sweep_visits = float(np.mean([s["sweep_visits"] for s in stats]))
+    relabel_visits = float(np.mean([s["relabel_visits"] for s in stats]))
+    alg_bytes = (BYTES_PER_NODE_SWEEP * sweep_visits + BYTES_PER_NODE_BFS * relabel_visits) \
+        * nodes_per_tile
+    solve_s = float(np.mean(solve_ms)) * 1e-3
+    achieved = alg_bytes / solve_s / 1e9
+
+    # ----- CPU oracle on the same pairs: baseline time and parity of the timed pairs -----
+    cpu = None
+    parity = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, refs = _cpu_baseline(wl, pairs)
+        ok_flow = ok_lab = True
+        for k, ref in enumerate(refs):
+            step(k)
+            torch.cuda.synchronize(dev)
+            ok_flow &= int(buf.flow.item()) == ref["flow"]
+            ok_lab &= bool(np.array_equal(buf.labels.cpu().numpy(), ref["labels"]))
+        parity = {"pairs": len(refs), "flow_equal": ok_flow, "labels_equal": ok_lab}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": _config(wl, {"sweeps_per_relabel": o.sweeps_per_relabel,
-                               "replicas": world}),
+                               "local_iters": o.local_iters, "relabel_passes": o.relabel_passes,
+                               "replicas": world, "tile": [ti["tile_w"], ti["tile_h"]]}),
         "e2e": e2e,
-        "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "hbm", "kernel": "k_solve_tiled", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _profiled_traffic(),
                      "peak_kind": f"{peak_kind} HBM copy",
-                     "bytes_per_launch": bytes_per_sweep,
-                     "avg_launch_us": sweep_launch_s * 1e6},
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": solve_s * 1e3,
+                     "accounting": "72 B/node per tile visit of a sweep round + 40 B/node per "
+                                   "tile visit of a relabel pass"},
+        "phases_ms": {"cost_volume+build": float(np.mean(build_ms)),
+                      "maxflow_solve": float(np.mean(solve_ms)),
+                      "extract_labels": float(np.mean(extract_ms))},
         "cpu_baseline": cpu,
+        "parity_vs_oracle": parity,
         "clocks": clk,
         "gpu_launches": int(launches),
-        "solver": {"sweeps_per_pair": sweeps / args.steps, "relabels_per_pair": relabels / args.steps,
-                   "bfs_passes_per_pair": passes / args.steps,
-                   "sweep_ms_per_pair": sweep_ns * 1e-6 / args.steps,
-                   "relabel_ms_per_pair": relabel_ns * 1e-6 / args.steps},
+        "solver": {k: float(np.mean([s[k] for s in stats])) for k in
+                   ("relabels", "sweeps", "bfs_passes", "label_passes", "sweep_visits",
+                    "relabel_visits")},
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -331,6 +388,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gazecut", choices=["gazecut", "reference"])
     ap.add_argument("--sweeps-per-relabel", type=int, default=8)
+    ap.add_argument("--local-iters", type=int, default=8)
+    ap.add_argument("--relabel-passes", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -94,8 +94,11 @@ typedef struct gs_solve_opts {
     int64_t max_iters;           /* cap on global relabels in exact mode (> 0) */
     int32_t local_iters;         /* TILED: push/relabel iterations per tile visit (0: 8) */
     int32_t relabel_passes;      /* TILED: tile passes of an intermediate global relabel
-                                    (0: 8); the relabel that decides termination always
+                                    (0: 4); the relabel that decides termination always
                                     runs to its fixed point */
+    int32_t tail_iters;          /* TILED: local iterations per tile visit once few nodes
+                                    are active (0: 4 x local_iters) */
+    int32_t reserved;            /* must be 0 */
 } gs_solve_opts;
 
 /* Derived sizes (0 when the params are invalid). */
@@ -161,12 +164,19 @@ GS_API int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opt
 GS_API int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, int64_t *energy,
               void *stream);
 
-/* Diagnostics of the last solve on this workspace: host int64[8] =
- * {global relabels, sweeps, BFS passes, label passes, active nodes at exit,
- *  device time of the push-relabel sweeps in ns, device time of the global
- *  relabels in ns, kernel launches of the solve}.  The two times are measured
- * with CUDA events on the solve's stream.  Synchronises `stream`. */
+/* Diagnostics of the last solve on this workspace: host int64[10] =
+ * {global relabels, sweep rounds, relabel passes, label-extraction passes,
+ *  active nodes at exit, device time of the sweep rounds in ns, device time
+ *  of the global relabels in ns, kernel launches of the solve, tile visits of
+ *  the sweep rounds, tile visits of the relabel passes}.  The times come from
+ * the device's global timer (TILED) or CUDA events on the solve's stream
+ * (SIMPLE); the visit counts are 0 for the SIMPLE engine.  Synchronises
+ * `stream`. */
 GS_API int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stream);
+
+/* Tile shape the TILED engine uses for these params: host int32[4] =
+ * {sites per tile along W, rows per tile, number of tiles, shared bytes}. */
+GS_API int gs_tile_info(const gs_params *p, int32_t *out);
 
 /* Number of kernels this library has launched in this process so far. */
 GS_API int64_t gs_kernel_launches(void);

@@ -261,6 +261,8 @@ int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     GS_CUDA_TRY(cudaMemcpyAsync(host_stats, c->stats, 8 * sizeof(long long),
                                 cudaMemcpyDeviceToHost, st));
+    GS_CUDA_TRY(cudaMemcpyAsync(host_stats + 8, &c->visits_sweep, 2 * sizeof(long long),
+                                cudaMemcpyDeviceToHost, st));
     GS_CUDA_TRY(cudaStreamSynchronize(st));
     return GS_OK;
 }

@@ -71,7 +71,9 @@ struct Ctrl {
     long long stats[8];   // relabels, sweeps, bfs passes, label passes, active at exit,
                           // sweep ns, relabel ns, launches
     unsigned long long deficit_left;
-    unsigned long long pad2[3];
+    long long visits_sweep;    // tile visits of the sweep rounds (all blocks)
+    long long visits_relabel;  // tile visits of the relabel passes (all blocks)
+    unsigned long long pad2;
 };
 static_assert(sizeof(Ctrl) <= 256, "ctrl block");
 

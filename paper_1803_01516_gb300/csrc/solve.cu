@@ -164,6 +164,8 @@ extern "C" int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_
     if (make_geom(p, &g) != GS_OK || !o || !graph || !workspace || !status) return GS_ERR_INVAL;
     if (o->sweeps_per_relabel < 1 || o->max_iters < 1) return GS_ERR_INVAL;
     if (o->engine != GS_ENGINE_TILED && o->engine != GS_ENGINE_SIMPLE) return GS_ERR_INVAL;
+    if (o->reserved != 0 || o->local_iters < 0 || o->relabel_passes < 0 || o->tail_iters < 0)
+        return GS_ERR_INVAL;
     if (o->mode != GS_MODE_EXACT && o->mode != GS_MODE_FIXED_SWEEPS) return GS_ERR_INVAL;
     if (o->mode == GS_MODE_FIXED_SWEEPS && o->fixed_sweeps < 0) return GS_ERR_INVAL;
     if (((uintptr_t)workspace & 255) != 0) return GS_ERR_INVAL;

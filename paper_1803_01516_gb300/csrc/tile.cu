@@ -57,7 +57,7 @@ struct SolveArgs {
     int dir;             // 0: distance to sink capacity over out-arcs (heights);
                          // 1: distance from positive excess over in-arcs (reachability)
     Ctrl *ctrl;
-    int mode, sweeps_per_relabel, local_iters, relabel_passes;
+    int mode, sweeps_per_relabel, local_iters, relabel_passes, tail_iters;
     long long fixed_sweeps, max_iters;
 };
 
@@ -231,8 +231,11 @@ __device__ __forceinline__ int32_t smem_residual(const TileSmem &m, const TileGe
 
 // Apply a push of d along slot q to the residual words in shared memory; when
 // the word belongs to a halo node (slots whose residual is stored at the arc's
-// head), the global copy is updated at once as well.  Returns the grown value
-// of a word that increased (for overflow detection).
+// head), the global copy is updated at once as well.  Only the data-arc
+// residual can grow without a bound of its own (flow pushed back along the
+// infinite reverse arc); its new value is returned for the overflow check.
+// Every other word is a residual of an arc pair and stays within the pair's
+// capacity, so those updates need no returned value.
 __device__ __forceinline__ int32_t smem_push_residual(const TileSmem &m, const TileGeom &t,
                                                       const State &s, int pi, int64_t gi,
                                                       const Geom &g, int q, int32_t d,
@@ -243,27 +246,33 @@ __device__ __forceinline__ int32_t smem_push_residual(const TileSmem &m, const T
         case 2: atomicSub(&m.rr[pi], d); return 0;
         case 3:
             if (head_is_halo) atomicAdd(&s.rr[gi - 1], d);
-            return atomicAdd(&m.rr[pi - 1], d) + d;
+            atomicAdd(&m.rr[pi - 1], d);
+            return 0;
         case 4: atomicSub(&m.rd[pi], d); return 0;
         case 5:
             if (head_is_halo) atomicAdd(&s.rd[gi - g.SY], d);
-            return atomicAdd(&m.rd[pi - t.SYs], d) + d;
+            atomicAdd(&m.rd[pi - t.SYs], d);
+            return 0;
         case 6: atomicSub(&m.ri0[pi], d); return 0;
         case 7: atomicSub(&m.ri1[pi], d); return 0;
         case 8: atomicSub(&m.ri2[pi], d); return 0;
         case 9: atomicSub(&m.ri3[pi], d); return 0;
         case 10:
             if (head_is_halo) atomicAdd(&s.ri1[gi - 1 + g.P], d);
-            return atomicAdd(&m.ri1[pi - 1 + t.SJ], d) + d;
+            atomicAdd(&m.ri1[pi - 1 + t.SJ], d);
+            return 0;
         case 11:
             if (head_is_halo) atomicAdd(&s.ri0[gi + 1 + g.P], d);
-            return atomicAdd(&m.ri0[pi + 1 + t.SJ], d) + d;
+            atomicAdd(&m.ri0[pi + 1 + t.SJ], d);
+            return 0;
         case 12:
             if (head_is_halo) atomicAdd(&s.ri3[gi - g.SY + g.P], d);
-            return atomicAdd(&m.ri3[pi - t.SYs + t.SJ], d) + d;
+            atomicAdd(&m.ri3[pi - t.SYs + t.SJ], d);
+            return 0;
         default:
             if (head_is_halo) atomicAdd(&s.ri2[gi + g.SY + g.P], d);
-            return atomicAdd(&m.ri2[pi + t.SYs + t.SJ], d) + d;
+            atomicAdd(&m.ri2[pi + t.SYs + t.SJ], d);
+            return 0;
     }
 }
 
@@ -354,6 +363,9 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
     for (int q = 0; q < kSlots; q++) off[q] = soff(t, q);
     for (int w = threadIdx.x; w < 3 * (kMaxRows / 32); w += blockDim.x) (&dirty[0][0])[w] = 0;
     __syncthreads();
+    int row[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; k++) row[k] = (threadIdx.x + k * blockDim.x) / t.TW;
     bool any_change = false;
     for (int iter = 0;; iter++) {
         const unsigned *cur = dirty[iter % 3];
@@ -364,7 +376,7 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
 #pragma unroll
         for (int k = 0; k < NPT; k++) {
             if (pi[k] < 0) continue;
-            const int r = (threadIdx.x + k * blockDim.x) / t.TW;
+            const int r = row[k];
             if (iter > 0) {
                 bool dep = false;
 #pragma unroll
@@ -569,13 +581,17 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
 
 // Up to local_iters push/relabel iterations of one tile in shared memory.
 template <int NPT>
-__device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round,
+__device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round, int iters,
                            int &overflow) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
     int32_t *act_next = a.tile_act + ((round + 1) & 1) * t.T;
+    // per own node: shared index, coordinates in the tile and existing arcs,
+    // so the discharge loop needs no divisions
+    __shared__ uint32_t s_info[kMaxTileNodes];
+    __shared__ uint16_t s_exb[kMaxTileNodes];
     load_halo(a, m, o, true, s.ht);
     int pi[NPT];
     int64_t gi[NPT];
@@ -601,6 +617,8 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
         pi[k] = p;
         gi[k] = i;
         ex_bits[k] = arc_exists(g, y, j, W);
+        s_info[n] = (uint32_t)p | ((uint32_t)wl << 16) | ((uint32_t)yl << 21) | ((uint32_t)j << 25);
+        s_exb[n] = (uint16_t)ex_bits[k];
         m.ex[p] = o_ex[k] = ld(&s.ex[i]);
         m.ht[p] = o_ht[k] = ld(&s.ht[i]);
         m.rc[p] = o_rc[k] = ld(&s.rc[i]);
@@ -626,11 +644,12 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     // warps do not idle on inactive lanes.
     __shared__ int s_nact[2];
     __shared__ uint16_t s_list[kMaxTileNodes];
+    const int64_t tile_g0 = (int64_t)o.y0 * g.SY + o.W0;
     if (threadIdx.x == 0) s_nact[0] = s_nact[1] = 0;
     __syncthreads();
     unsigned nb_touch = 0;   // bit 0: left, 1: right, 2: up, 3: down neighbour tile received flow
     const int lane = threadIdx.x & 31;
-    for (int it = 0; it < a.local_iters; it++) {
+    for (int it = 0; it < iters; it++) {
         int *cnt = &s_nact[it & 1];
 #pragma unroll
         for (int k = 0; k < NPT; k++) {
@@ -650,11 +669,12 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
         if (nact == 0) break;
         for (int li = threadIdx.x; li < nact; li += blockDim.x) {
             const int n = s_list[li];
-            const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
-            const int W = o.W0 + wl, y = o.y0 + yl;
-            const int p = pidx(t, yl, j, wl);
-            const int64_t gin = ((int64_t)y * g.K + j) * g.P + W;
-            const unsigned exb = arc_exists(g, y, j, W);
+            const uint32_t info = s_info[n];
+            const int p = (int)(info & 0xffffu);
+            const int wl = (int)((info >> 16) & 31u), yl = (int)((info >> 21) & 15u);
+            const int j = (int)(info >> 25);
+            const int64_t gin = tile_g0 + (int64_t)yl * g.SY + (int64_t)j * g.P + wl;
+            const unsigned exb = s_exb[n];
             const int32_t e = m.ex[p];
             const int32_t hu = m.ht[p];
             if (e <= 0 || hu >= kInfH) continue;
@@ -675,13 +695,13 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
                     const bool halo = wl2 < 0 || wl2 >= t.TW || yl2 < 0 || yl2 >= t.TH;
                     const int32_t grown = smem_push_residual(m, t, s, p, gin, g, q, d, halo);
                     overflow |= grown > kCapLimit;
+                    // an excess never exceeds the total source capacity (<= 2^30,
+                    // checked when the graph is built): no overflow check needed
                     if (halo) {
-                        const int32_t ev = atomicAdd(&s.ex[gin + goff[q]], d) + d;
-                        overflow |= ev > kCapLimit;
+                        atomicAdd(&s.ex[gin + goff[q]], d);
                         nb_touch |= wl2 < 0 ? 1u : wl2 >= t.TW ? 2u : yl2 < 0 ? 4u : 8u;
                     } else {
-                        const int32_t ev = atomicAdd(&m.ex[p + off[q]], d) + d;
-                        overflow |= ev > kCapLimit;
+                        atomicAdd(&m.ex[p + off[q]], d);
                     }
                     rr[q] -= d;
                     left -= d;
@@ -743,6 +763,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
     Ctrl *ctrl = a.ctrl;
     const int T = a.t.T;
     long long relabels = 0, rounds = 0, passes = 0, visits = 0, sweep_visits = 0;
+    long long my_sweep_visits = 0;
+    const unsigned long long t_start = now_ns();
+    long long relabel_ns_local = 0;
     unsigned long long t_relabel = 0, t_sweep = 0;
     long long active = 0;
     int converged = 0, overflow = 0, full = 0;
@@ -754,6 +777,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
         long long cnt = 0;
         for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
             cnt += relabel_init_tile<NPT>(a, m, tile);
+            visits++;
             if (threadIdx.x == 0) {
                 __stcg(&a.tile_dirty[tile], 0);
                 __stcg(&a.tile_dirty[T + tile], 0);
@@ -804,6 +828,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
             log[4 * relabels + 2] = sweep_visits;
             log[4 * relabels + 3] = (long long)(now_ns() - t0);
         }
+        // the relabel's duration as block 0 saw it, shared through the next barrier sum
+        relabel_ns_local = (long long)(now_ns() - t0);
         relabels++;
         t_relabel += now_ns() - t0;
         if (aborted(ctrl)) break;
@@ -820,13 +846,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
         // relabel follows every sweeps_per_relabel rounds; in the tail (few
         // active nodes, cheap rounds) up to 8x as many; rounds stop early once
         // no tile has work.
-        long long n = active * 64 > (long long)a.g.N ? a.sweeps_per_relabel
-                                                      : 8ll * a.sweeps_per_relabel;
+        const bool tail = active * 64 <= (long long)a.g.N;
+        long long n = tail ? 64ll * a.sweeps_per_relabel : a.sweeps_per_relabel;
+        const long long last_relabel_ns =
+            grid_sync_sum(ctrl, (blockIdx.x == 0 && threadIdx.x == 0) ? relabel_ns_local : 0);
+        const int iters = tail ? a.tail_iters : a.local_iters;
         if (a.mode == GS_MODE_FIXED_SWEEPS) {
             n = min(n, a.fixed_sweeps - rounds);
             if (n <= 0) break;
         }
         t0 = now_ns();
+        long long prev1_worked = 1ll << 40, prev2_worked = 1ll << 40;
         for (long long r = 0; r < n; r++) {
             const int cur = (int)(r & 1);
             long long worked = 0;
@@ -837,21 +867,42 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
                 __syncthreads();
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
                 if (s_work) {
-                    sweep_tile<NPT>(a, m, tile, cur, overflow);
+                    sweep_tile<NPT>(a, m, tile, cur, iters, overflow);
                     worked++;
+                    my_sweep_visits++;
                 }
             }
-            const long long tot_worked = grid_sync_sum(ctrl, threadIdx.x == 0 ? worked : 0);
+            // block 0's clock rides along the grid sum so every block takes the same
+            // decision: in the tail, sweep on until the rounds have cost as much as
+            // the last relabel and the number of tiles with work stopped falling
+            // (the excess left is circling on stale heights)
+            const Sum2 rs = grid_sync_sum2(
+                ctrl, threadIdx.x == 0 ? worked : 0,
+                (blockIdx.x == 0 && threadIdx.x == 0) ? (long long)(now_ns() - t0) : 0);
+            const long long tot_worked = rs.a;
+            const bool stalled = tail && r >= 2 && tot_worked * 10 > prev2_worked * 9 &&
+                                 rs.b > last_relabel_ns;
+            prev2_worked = prev1_worked;
+            prev1_worked = tot_worked;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && rounds < 4096) {
+                // per-round log after the per-relabel log: tiles worked, end time
+                long long *log = (long long *)a.log + 1024;
+                log[2 * rounds + 0] = tot_worked | ((long long)relabels << 32);
+                log[2 * rounds + 1] = (long long)(now_ns() - t_start);
+            }
             rounds++;
             sweep_visits += tot_worked;
-            if (aborted(ctrl) || tot_worked == 0) break;
+            if (aborted(ctrl) || tot_worked == 0 || stalled) break;
         }
         t_sweep += now_ns() - t0;
         if (aborted(ctrl)) break;
     }
     if (__syncthreads_or(overflow) && threadIdx.x == 0)
         atomicCAS(&ctrl->status, GS_OK, GS_ERR_OVERFLOW);
-    if (threadIdx.x == 0) atomicAdd((unsigned long long *)&ctrl->stats[3], (unsigned long long)visits);
+    if (threadIdx.x == 0) {
+        atomicAdd((unsigned long long *)&ctrl->visits_relabel, (unsigned long long)visits);
+        atomicAdd((unsigned long long *)&ctrl->visits_sweep, (unsigned long long)my_sweep_visits);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->stats[0] = relabels;
         ctrl->stats[1] = rounds;
@@ -1042,6 +1093,7 @@ int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opt
     a.sweeps_per_relabel = o->sweeps_per_relabel;
     a.local_iters = o->local_iters > 0 ? o->local_iters : 8;
     a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 4;
+    a.tail_iters = o->tail_iters > 0 ? o->tail_iters : 4 * a.local_iters;
     a.fixed_sweeps = o->fixed_sweeps;
     a.max_iters = o->max_iters;
     GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
@@ -1075,3 +1127,17 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
 }
 
 }  // namespace gs
+
+extern "C" int gs_tile_info(const gs_params *p, int32_t *out) {
+    gs::Geom g;
+    if (gs::make_geom(p, &g) != GS_OK || !out) return GS_ERR_INVAL;
+    gs::TileGeom t;
+    int npt;
+    size_t smem;
+    if (!gs::pick_tile(g, t, npt, smem)) return GS_ERR_INVAL;
+    out[0] = t.TW;
+    out[1] = t.TH;
+    out[2] = t.T;
+    out[3] = (int32_t)smem;
+    return GS_OK;
+}

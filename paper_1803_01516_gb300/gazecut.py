@@ -29,7 +29,7 @@ EXPORTS = [
     "gs_num_sites_w", "gs_cost_volume_bytes", "gs_graph_bytes", "gs_workspace_bytes",
     "gs_num_nodes", "gs_stereo_cost_volume", "gs_build_graph", "gs_maxflow_solve",
     "gs_extract_labels", "gs_energy", "gs_solve_stats", "gs_kernel_launches",
-    "gs_noalloc_scratch_bytes", "gs_maxflow_solve_noalloc",
+    "gs_noalloc_scratch_bytes", "gs_maxflow_solve_noalloc", "gs_tile_info",
 ]
 
 
@@ -43,7 +43,8 @@ class GsSolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sweeps_per_relabel", ctypes.c_int32),
                 ("fixed_sweeps", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("local_iters", ctypes.c_int32),
-                ("relabel_passes", ctypes.c_int32)]
+                ("relabel_passes", ctypes.c_int32), ("tail_iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 @dataclass
@@ -80,10 +81,12 @@ class SolveOpts:
     engine: int = GS_ENGINE_TILED
     local_iters: int = 0          # 0: library default
     relabel_passes: int = 0       # 0: library default
+    tail_iters: int = 0           # 0: library default
 
     def c(self) -> GsSolveOpts:
         return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, self.engine,
-                           self.max_iters, self.local_iters, self.relabel_passes)
+                           self.max_iters, self.local_iters, self.relabel_passes,
+                           self.tail_iters, 0)
 
 
 _lib = None
@@ -114,6 +117,7 @@ def lib():
             "gs_solve_stats": ([P, P, P], ctypes.c_int),
             "gs_kernel_launches": ([], I64),
             "gs_noalloc_scratch_bytes": ([], SZ),
+            "gs_tile_info": ([pp, P], ctypes.c_int),
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -215,16 +219,22 @@ def gs_energy(cost: torch.Tensor, labels: torch.Tensor, p: Params, energy: torch
 
 
 def gs_solve_stats(workspace: torch.Tensor, stream=None) -> dict:
-    out = (ctypes.c_int64 * 8)()
+    out = (ctypes.c_int64 * 10)()
     rc = lib().gs_solve_stats(_dev(workspace, torch.uint8, "workspace"), out, _stream(stream))
     _check(rc, "gs_solve_stats")
     keys = ["relabels", "sweeps", "bfs_passes", "label_passes", "active_at_exit", "sweep_ns",
-            "relabel_ns", "launches"]
+            "relabel_ns", "launches", "sweep_visits", "relabel_visits"]
     return {k: int(out[i]) for i, k in enumerate(keys)}
 
 
 def gs_kernel_launches() -> int:
     return int(lib().gs_kernel_launches())
+
+
+def gs_tile_info(p: Params) -> dict:
+    out = (ctypes.c_int32 * 4)()
+    _check(lib().gs_tile_info(ctypes.byref(p.c()), out), "gs_tile_info")
+    return {"tile_w": out[0], "tile_h": out[1], "tiles": out[2], "smem_bytes": out[3]}
 
 
 def gs_noalloc_scratch_bytes() -> int:
