@@ -159,6 +159,50 @@ GS_API int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_opts
 GS_API int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, void *workspace,
                       int32_t *labels, int64_t *flow, int32_t *status, void *stream);
 
+/*
+ * Learned data term (the paper's g_v generalised to a trainable matching cost;
+ * the paper tunes h~1 by grid search, §4.3): at every cross point
+ *   c = w1 |L - R| + w2 |dxL - dxR|,  dx = central difference with replicated
+ *   border,  cost = rint(scale * min(c, tau))   (round half to even)
+ * computed in FP32 with every product and sum rounded separately (no fused
+ * multiply-add).  Layout and arguments as gs_stereo_cost_volume; w1, w2,
+ * tau >= 0, scale > 0; GS_ERR_OVERFLOW when scale * tau > 2^30.
+ */
+GS_API int gs_stereo_cost_volume_f32(const uint8_t *L, const uint8_t *R, int32_t pitch,
+                                     const gs_params *p, float w1, float w2, float tau, float scale,
+                                     int32_t *cost, void *stream);
+
+/*
+ * Adjoint of the minimum energy E* (§2) at a minimiser X (int32 [h][n_g]):
+ *   dE/dC[v][l] = [X_v = l]; written as grad * one-hot into dcost (float
+ *   [h][n_g][D]) when dcost is not NULL;
+ *   counts (device int64[2]) = { sum |X_u - X_v| = dE/dlambda,
+ *                                sum (|X_u - X_v| - 1)_+ = dE/dinhibit }
+ *   over the 4-connected pairs (vertical pairs in the second sum only when
+ *   vertical_inhibit).  E* is concave and piecewise linear in the costs and
+ *   weights: these are its gradients where the minimiser is unique.
+ */
+GS_API int gs_energy_backward(const int32_t *labels, const gs_params *p, float grad, float *dcost,
+                              int64_t *counts, void *stream);
+
+/*
+ * Chain rule through gs_stereo_cost_volume_f32 at the labels X: device
+ * int64[3] = { sum_v |L - R| [c < tau], sum_v 2 |dxL - dxR| [c < tau],
+ *              sum_v [c >= tau] }, c taken at (v, X_v).  With the quantiser
+ * treated as the identity, dE/dw1 = sums[0], dE/dw2 = sums[1] / 2,
+ * dE/dtau = sums[2] (energy in cost units).
+ */
+GS_API int gs_cost_volume_f32_backward(const uint8_t *L, const uint8_t *R, int32_t pitch,
+                                       const gs_params *p, float w1, float w2, float tau,
+                                       const int32_t *labels, int64_t *sums, void *stream);
+
+/* cost[v][labels[v]] += value for every site (labels outside [0, D) are
+ * skipped): the loss augmentation of structured learning, where adding a
+ * constant to the ground-truth label's cost equals subtracting the Hamming
+ * loss up to a constant. */
+GS_API int gs_cost_add_at_labels(int32_t *cost, const int32_t *labels, const gs_params *p,
+                                 int32_t value, void *stream);
+
 /* E(X) of §2 for labels int32 [h][n_g] over cost [h][n_g][D]; energy: device int64[1],
  * negative if a label lies outside [0, D). */
 GS_API int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, int64_t *energy,

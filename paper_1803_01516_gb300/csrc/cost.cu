@@ -188,3 +188,197 @@ int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, in
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- learned data term (FP32) ---
+//
+// c = w1 |L - R| + w2 |dxL - dxR| at the cross point, truncated at tau, then
+// quantised to int32 at `scale` (round half to even).  dx is the central
+// difference (I[x+1] - I[x-1]) / 2 with replicated borders.  Every product and
+// sum is rounded separately (no fused multiply-add) so that the host reference
+// computes the same integers.
+
+namespace gs {
+
+__device__ __forceinline__ float dx_at(const uint8_t *row, int x, int w) {
+    const int xm = x > 0 ? x - 1 : 0, xp = x < w - 1 ? x + 1 : w - 1;
+    return __fmul_rn(0.5f, (float)((int)row[xp] - (int)row[xm]));
+}
+
+// features of cross point (W, S) in row y: a = |L - R|, b = |dxL - dxR|
+__device__ __forceinline__ void cross_features(const uint8_t *Lrow, const uint8_t *Rrow, int w,
+                                               int W, int S, int dis0, float &fa, float &fb) {
+    const int xr = W + S, xl = W + dis0 - S;
+    fa = fabsf((float)((int)Lrow[xl] - (int)Rrow[xr]));
+    fb = fabsf(__fsub_rn(dx_at(Lrow, xl, w), dx_at(Rrow, xr, w)));
+}
+
+__device__ __forceinline__ float learned_cost(float fa, float fb, float w1, float w2, float tau) {
+    const float c = __fadd_rn(__fmul_rn(w1, fa), __fmul_rn(w2, fb));
+    return fminf(c, tau);
+}
+
+__global__ void k_cost_volume_f32(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R,
+                                  int pitch, int w, int ng, int D, int dis0, float w1, float w2,
+                                  float tau, float scale, int32_t *__restrict__ cost) {
+    const int y = blockIdx.y;
+    const uint8_t *Lrow = L + (size_t)y * pitch, *Rrow = R + (size_t)y * pitch;
+    const int n = ng * D;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int W = e / D, S = e - W * D;
+        float fa, fb;
+        cross_features(Lrow, Rrow, w, W, S, dis0, fa, fb);
+        const float c = learned_cost(fa, fb, w1, w2, tau);
+        cost[(size_t)y * n + e] = __float2int_rn(__fmul_rn(scale, c));
+    }
+}
+
+// Chain rule through the learned cost at the chosen labels: exact integer sums
+//   out[0] = sum_v |L - R| [c < tau],  out[1] = sum_v 2|dxL - dxR| [c < tau],
+//   out[2] = sum_v [c >= tau]
+// (c at the label X_v).  dE/dw1 = out[0], dE/dw2 = out[1] / 2, dE/dtau = out[2]
+// for the energy in cost units, the quantiser taken as the identity.
+__global__ void k_cost_f32_backward(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R,
+                                    int pitch, int w, int ng, int h, int D, int dis0, float w1,
+                                    float w2, float tau, const int32_t *__restrict__ X,
+                                    unsigned long long *__restrict__ out) {
+    unsigned long long sa = 0, sb = 0, st = 0;
+    const long long sites = (long long)ng * h;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < sites;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int W = (int)(v % ng), y = (int)(v / ng);
+        const int S = min(max(X[v], 0), D - 1);
+        float fa, fb;
+        cross_features(L + (size_t)y * pitch, R + (size_t)y * pitch, w, W, S, dis0, fa, fb);
+        const float c = __fadd_rn(__fmul_rn(w1, fa), __fmul_rn(w2, fb));
+        if (c < tau) {
+            sa += (unsigned long long)fa;
+            sb += (unsigned long long)(2.0f * fb);
+        } else {
+            st += 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+        st += __shfl_down_sync(0xffffffffu, st, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (sa) atomicAdd(&out[0], sa);
+        if (sb) atomicAdd(&out[1], sb);
+        if (st) atomicAdd(&out[2], st);
+    }
+}
+
+// Adjoint of the minimum energy (§2) at the minimiser X: dE/dC[v][l] = [X_v = l]
+// (written as grad * one-hot when dcost is given), dE/dlambda = sum |X_u - X_v|,
+// dE/dinhibit = sum (|X_u - X_v| - 1)_+ over the pairs that carry the inhibit
+// term.  E* is concave and piecewise linear in (C, lambda, inhibit); these are
+// its gradients where X is the unique minimiser, and supergradients otherwise.
+__global__ void k_energy_backward(const int32_t *__restrict__ X, int ng, int h, int D, int vinh,
+                                  float grad, float *__restrict__ dcost,
+                                  unsigned long long *__restrict__ counts) {
+    unsigned long long jumps = 0, viol = 0;
+    const long long sites = (long long)ng * h;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < sites;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int W = (int)(v % ng), y = (int)(v / ng);
+        const int a = X[v];
+        if (dcost)
+            for (int l = 0; l < D; l++) dcost[v * D + l] = l == a ? grad : 0.0f;
+        if (W + 1 < ng) {
+            const int d = abs(a - X[v + 1]);
+            jumps += d;
+            viol += d > 1 ? d - 1 : 0;
+        }
+        if (y + 1 < h) {
+            const int d = abs(a - X[v + ng]);
+            jumps += d;
+            if (vinh) viol += d > 1 ? d - 1 : 0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        jumps += __shfl_down_sync(0xffffffffu, jumps, o);
+        viol += __shfl_down_sync(0xffffffffu, viol, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (jumps) atomicAdd(&counts[0], jumps);
+        if (viol) atomicAdd(&counts[1], viol);
+    }
+}
+
+}  // namespace gs
+
+extern "C" {
+
+int gs_stereo_cost_volume_f32(const uint8_t *L, const uint8_t *R, int32_t pitch, const gs_params *p,
+                              float w1, float w2, float tau, float scale, int32_t *cost,
+                              void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !L || !R || !cost || pitch < p->w) return GS_ERR_INVAL;
+    if (!(scale > 0.0f) || !(tau >= 0.0f) || !(w1 >= 0.0f) || !(w2 >= 0.0f)) return GS_ERR_INVAL;
+    if ((double)scale * tau > (double)(1 << 30)) return GS_ERR_OVERFLOW;
+    dim3 grid((g.ng * g.D + 255) / 256, g.h);
+    k_cost_volume_f32<<<grid, 256, 0, (cudaStream_t)stream>>>(L, R, pitch, p->w, g.ng, g.D,
+                                                              p->dis0, w1, w2, tau, scale, cost);
+    count_launches(1);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_cost_volume_f32_backward(const uint8_t *L, const uint8_t *R, int32_t pitch,
+                                const gs_params *p, float w1, float w2, float tau,
+                                const int32_t *labels, int64_t *sums, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !L || !R || !labels || !sums || pitch < p->w)
+        return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemsetAsync(sums, 0, 3 * sizeof(int64_t), st));
+    const long long sites = (long long)g.ng * g.h;
+    const int blocks = (int)std::min<long long>((sites + 255) / 256, 4 * 152);
+    k_cost_f32_backward<<<blocks, 256, 0, st>>>(L, R, pitch, p->w, g.ng, g.h, g.D, p->dis0, w1, w2,
+                                               tau, labels, (unsigned long long *)sums);
+    count_launches(1);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_energy_backward(const int32_t *labels, const gs_params *p, float grad, float *dcost,
+                       int64_t *counts, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !labels || !counts) return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * sizeof(int64_t), st));
+    const long long sites = (long long)g.ng * g.h;
+    const int blocks = (int)std::min<long long>((sites + 255) / 256, 16 * 152);
+    k_energy_backward<<<blocks, 256, 0, st>>>(labels, g.ng, g.h, g.D, p->vertical_inhibit ? 1 : 0,
+                                             grad, dcost, (unsigned long long *)counts);
+    count_launches(1);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // extern "C"
+
+// Loss augmentation for structured learning: cost[v][labels[v]] += value.
+namespace gs {
+__global__ void k_cost_add_at_labels(int32_t *__restrict__ cost, const int32_t *__restrict__ X,
+                                     long long sites, int D, int32_t value) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < sites;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int a = X[v];
+        if (a >= 0 && a < D) cost[v * D + a] += value;
+    }
+}
+}  // namespace gs
+
+extern "C" int gs_cost_add_at_labels(int32_t *cost, const int32_t *labels, const gs_params *p,
+                                     int32_t value, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !cost || !labels) return GS_ERR_INVAL;
+    const long long sites = (long long)g.ng * g.h;
+    const int blocks = (int)std::min<long long>((sites + 255) / 256, 16 * 152);
+    k_cost_add_at_labels<<<blocks, 256, 0, (cudaStream_t)stream>>>(cost, labels, sites, g.D, value);
+    count_launches(1);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}

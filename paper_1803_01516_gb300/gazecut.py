@@ -30,6 +30,8 @@ EXPORTS = [
     "gs_num_nodes", "gs_stereo_cost_volume", "gs_build_graph", "gs_maxflow_solve",
     "gs_extract_labels", "gs_energy", "gs_solve_stats", "gs_kernel_launches",
     "gs_noalloc_scratch_bytes", "gs_maxflow_solve_noalloc", "gs_tile_info",
+    "gs_stereo_cost_volume_f32", "gs_energy_backward", "gs_cost_volume_f32_backward",
+    "gs_cost_add_at_labels",
 ]
 
 
@@ -101,6 +103,7 @@ def lib():
                                "(the CUDA library has no CPU fallback)")
         L = ctypes.CDLL(LIB_PATH)
         P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        F = ctypes.c_float
         pp = ctypes.POINTER(GsParams)
         po = ctypes.POINTER(GsSolveOpts)
         sig = {
@@ -118,6 +121,10 @@ def lib():
             "gs_kernel_launches": ([], I64),
             "gs_noalloc_scratch_bytes": ([], SZ),
             "gs_tile_info": ([pp, P], ctypes.c_int),
+            "gs_stereo_cost_volume_f32": ([P, P, I32, pp, F, F, F, F, P, P], ctypes.c_int),
+            "gs_energy_backward": ([P, pp, F, P, P, P], ctypes.c_int),
+            "gs_cost_volume_f32_backward": ([P, P, I32, pp, F, F, F, P, P, P], ctypes.c_int),
+            "gs_cost_add_at_labels": ([P, P, pp, I32, P], ctypes.c_int),
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -209,6 +216,43 @@ def gs_extract_labels(graph: torch.Tensor, p: Params, o: SolveOpts, workspace: t
                                  _dev(labels, torch.int32, "labels"), _dev(flow, torch.int64, "flow"),
                                  _dev(status, torch.int32, "status"), _stream(stream))
     _check(rc, "gs_extract_labels")
+
+
+def gs_stereo_cost_volume_f32(L: torch.Tensor, R: torch.Tensor, p: Params, w1: float, w2: float,
+                              tau: float, scale: float, cost: torch.Tensor, stream=None):
+    if L.shape != (p.h, p.w) or R.shape != (p.h, p.w):
+        raise ValueError("L, R must be [h, w]")
+    if cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("cost has the wrong size")
+    rc = lib().gs_stereo_cost_volume_f32(_dev(L, torch.uint8, "L"), _dev(R, torch.uint8, "R"), p.w,
+                                         ctypes.byref(p.c()), w1, w2, tau, scale,
+                                         _dev(cost, torch.int32, "cost"), _stream(stream))
+    _check(rc, "gs_stereo_cost_volume_f32")
+
+
+def gs_energy_backward(labels: torch.Tensor, p: Params, grad: float, dcost, counts: torch.Tensor,
+                       stream=None):
+    dc = ctypes.c_void_p(0) if dcost is None else _dev(dcost, torch.float32, "dcost")
+    rc = lib().gs_energy_backward(_dev(labels, torch.int32, "labels"), ctypes.byref(p.c()), grad,
+                                  dc, _dev(counts, torch.int64, "counts"), _stream(stream))
+    _check(rc, "gs_energy_backward")
+
+
+def gs_cost_volume_f32_backward(L: torch.Tensor, R: torch.Tensor, p: Params, w1: float, w2: float,
+                                tau: float, labels: torch.Tensor, sums: torch.Tensor, stream=None):
+    rc = lib().gs_cost_volume_f32_backward(_dev(L, torch.uint8, "L"), _dev(R, torch.uint8, "R"),
+                                           p.w, ctypes.byref(p.c()), w1, w2, tau,
+                                           _dev(labels, torch.int32, "labels"),
+                                           _dev(sums, torch.int64, "sums"), _stream(stream))
+    _check(rc, "gs_cost_volume_f32_backward")
+
+
+def gs_cost_add_at_labels(cost: torch.Tensor, labels: torch.Tensor, p: Params, value: int,
+                          stream=None):
+    rc = lib().gs_cost_add_at_labels(_dev(cost, torch.int32, "cost"),
+                                     _dev(labels, torch.int32, "labels"), ctypes.byref(p.c()),
+                                     int(value), _stream(stream))
+    _check(rc, "gs_cost_add_at_labels")
 
 
 def gs_energy(cost: torch.Tensor, labels: torch.Tensor, p: Params, energy: torch.Tensor,
