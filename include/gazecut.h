@@ -218,6 +218,36 @@ GS_API int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params
  * `stream`. */
 GS_API int gs_solve_stats(const void *workspace, int64_t *host_stats, void *stream);
 
+/*
+ * Batched solve: n stereo pairs of any sizes and depth ranges (n <= 64), each
+ * through the whole path (data term, graph, exact max-flow, labels), with the
+ * max-flows of all pairs in ONE persistent cooperative launch and the label
+ * extractions in one more.  Pairs advance through their own relabel / sweep
+ * schedule inside the shared launch, so tiles of pairs still working fill
+ * the grid while others are done.  Every launch is stream-ordered with no host
+ * synchronisation, so the call can be captured in a CUDA graph.
+ * descs: HOST array of n descriptors whose pointers are device buffers sized
+ * by the single-pair queries; opts.engine must be GS_ENGINE_TILED.
+ * batch_workspace: gs_batch_workspace_bytes(n) device bytes (256-aligned).
+ * Results per pair as for gs_extract_labels; statistics via gs_solve_stats on
+ * the pair's workspace.
+ */
+typedef struct gs_pair_desc {
+    gs_params p;
+    gs_solve_opts o;
+    const uint8_t *L, *R;      /* device images, row pitch = p.w bytes */
+    int32_t *cost;             /* gs_cost_volume_bytes(&p) */
+    void *graph;               /* gs_graph_bytes(&p) */
+    void *workspace;           /* gs_workspace_bytes(&p, &o) */
+    int32_t *labels;           /* int32 [h][n_g] */
+    int64_t *flow;             /* int64 [1] */
+    int32_t *status;           /* int32 [1] */
+} gs_pair_desc;
+
+GS_API size_t gs_batch_workspace_bytes(int32_t n);
+GS_API int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batch_workspace,
+                            void *stream);
+
 /* Tile shape the TILED engine uses for these params: host int32[4] =
  * {sites per tile along W, rows per tile, number of tiles, shared bytes}. */
 GS_API int gs_tile_info(const gs_params *p, int32_t *out);

@@ -35,7 +35,7 @@ size_t graph_bytes(const Geom &g) {
 }
 
 size_t work_bytes(const Geom &g) {
-    return 256 + (size_t)round_up(g.N * sizeof(int32_t), 256) + tiled_work_extra(g);
+    return kWorkCtrlBytes + (size_t)round_up(g.N * sizeof(int32_t), 256) + tiled_work_extra(g);
 }
 
 State state_view(void *graph, const Geom &g) {
@@ -52,7 +52,7 @@ State state_view(void *graph, const Geom &g) {
 Work work_view(void *ws, const Geom &g) {
     Work w;
     w.ctrl = (Ctrl *)ws;
-    w.mark = (int32_t *)((char *)ws + 256);
+    w.mark = (int32_t *)((char *)ws + kWorkCtrlBytes);
     return w;
 }
 

@@ -77,6 +77,11 @@ struct Ctrl {
 };
 static_assert(sizeof(Ctrl) <= 256, "ctrl block");
 
+// Control region at the start of a workspace: the Ctrl block (256 bytes),
+// then the control words of the persistent kernel's grid barrier and
+// per-step sums.
+constexpr size_t kWorkCtrlBytes = 8192;
+
 struct Work {
     Ctrl *ctrl;
     int32_t *mark;

@@ -24,7 +24,8 @@
 // the excess and the residual its tile can see, and both only grow under
 // other tiles' updates, so the state stays a valid preflow; heights only steer
 // pushes.  The exit test is the exact reachability computed by the relabel.
-#include <cooperative_groups.h>
+#include <cstring>
+#include <mutex>
 
 #include "arcs.cuh"
 
@@ -52,11 +53,13 @@ struct SolveArgs {
     int32_t *tile_act;   // [2][T] tiles with work in the current / next sweep round
     int32_t *tile_dirty; // [2][T] tiles whose halo heights changed in the last relabel pass
     int32_t *tile_cnt;   // [T] active nodes per tile after its last relabel pass
-    void *log;           // diagnostics: per-relabel counters (label-mark buffer)
     int32_t *hgt;        // distances the relabel passes compute (state heights, or marks)
     int dir;             // 0: distance to sink capacity over out-arcs (heights);
                          // 1: distance from positive excess over in-arcs (reachability)
-    Ctrl *ctrl;
+    Ctrl *ctrl;          // the pair's control block (statistics)
+    int32_t *status;     // the caller's device status word
+    int32_t *labels;     // label extraction output [h][n_g]
+    int64_t *flow;       // label extraction output [1]
     int mode, sweeps_per_relabel, local_iters, relabel_passes, tail_iters;
     long long fixed_sweeps, max_iters;
 };
@@ -754,50 +757,233 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     __syncthreads();
 }
 
-// ------------------------------------------------------------ the solve ---
+// ------------------------------------------------------- the solve loop ---
+//
+// One cooperative launch solves n independent pairs.  The grid walks the
+// concatenated tiles of all pairs in steps separated by grid barriers; in a
+// step every tile does the work of its pair's current phase:
+//
+//   INIT   first relabel pass (masks, heights reset, in-tile distances)
+//   PASS   later relabel pass (all tiles once, then tiles whose halo changed)
+//   SWEEP  one sweep round over the tiles with work
+//   DONE   nothing
+//
+// After each barrier every block advances every pair's state machine from the
+// same per-pair sums (so all blocks take the same decisions) -- a pair that is
+// in its tail no longer leaves the grid idle when others still have work.
+// Per pair the schedule is the one of a single solve: a relabel (capped at
+// relabel_passes passes unless it decides termination), then sweep rounds --
+// sweeps_per_relabel of them, or in the tail (few active nodes) until the
+// tiles with work stop decreasing and the sweep rounds have cost as much as the
+// relabel did, both counted in tile visits one CTA makes in sequence.
+
+constexpr int kMaxPairs = 64;
+enum { PH_INIT = 0, PH_PASS = 1, PH_SWEEP = 2, PH_LABELS = 3, PH_DONE = 4 };
+
+struct PairState {
+    int phase, pass, full, conv, tail, status;
+    long long round, nrounds, rounds_total, relabels, passes, outer;
+    long long active, prev1, prev2, relabel_visits, relabel_depth, last_relabel_depth, sweep_depth;
+    long long visits_sweep_total, visits_relabel_total;
+};
+
+struct BatchArgs {
+    int n;            // pairs
+    int T_total;      // tiles over all pairs
+    int extract;      // 0: max-flow solve, 1: label extraction
+    int tile_off[kMaxPairs + 1];
+    Ctrl *bar;        // grid barrier and abort flag
+    long long *red;   // per-step, per-pair sums [3][n][4]
+    SolveArgs pair[kMaxPairs];
+};
+
+static_assert(sizeof(BatchArgs) <= 32000, "the batch arguments travel as kernel parameters");
+
+__device__ __forceinline__ int pair_of(const BatchArgs &B, int gt) {
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.tile_off[mid] <= gt) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ void start_relabel(PairState &st, const SolveArgs &a) {
+    if (a.mode == GS_MODE_EXACT && st.outer >= a.max_iters) {
+        st.phase = PH_DONE;
+        st.status = GS_ERR_TIMEOUT;
+        return;
+    }
+    st.outer++;
+    st.phase = PH_INIT;
+    st.relabel_visits = 0;
+    st.relabel_depth = 0;
+}
+
+// Critical-path cost of a step that visited `visits` tiles of a pair: the
+// number of tile visits one CTA makes in sequence, at least one.
+__device__ __forceinline__ long long step_depth(long long visits) {
+    return max(1ll, (visits + gridDim.x - 1) / gridDim.x);
+}
+
+// Advance one pair after a barrier; v = this step's sums {a, b, c, overflow}.
+__device__ void advance(PairState &st, const SolveArgs &a, const long long v[4], int extract) {
+    if (v[3] && st.status == GS_OK) {
+        st.status = GS_ERR_OVERFLOW;
+        st.phase = PH_DONE;
+        return;
+    }
+    switch (st.phase) {
+        case PH_INIT:
+            st.active = v[0];
+            st.relabel_visits = v[2];
+            st.relabel_depth = step_depth(v[2]);
+            st.passes++;
+            st.pass = 1;
+            st.phase = PH_PASS;
+            break;
+        case PH_PASS: {
+            st.active += v[0];
+            st.relabel_visits += v[2];
+            st.relabel_depth += step_depth(v[2]);
+            st.passes++;
+            bool end = false;
+            st.conv = 0;
+            if (v[1] == 0) {
+                st.conv = 1;
+                end = true;
+            } else if (!extract && !st.full && st.pass >= a.relabel_passes) {
+                end = true;
+            } else {
+                st.pass++;
+            }
+            if (!end) break;
+            if (extract) {
+                st.phase = PH_LABELS;
+                break;
+            }
+            st.relabels++;
+            st.last_relabel_depth = st.relabel_depth;
+            st.visits_relabel_total += st.relabel_visits;
+            if (st.active == 0) {
+                if (st.conv) {
+                    st.phase = PH_DONE;
+                } else {
+                    st.full = 1;     // nothing active within reach: decide with an exact relabel
+                    start_relabel(st, a);
+                }
+                break;
+            }
+            st.full = 0;
+            st.tail = st.active * 64 <= (long long)a.g.N;
+            st.nrounds = st.tail ? 64ll * a.sweeps_per_relabel : a.sweeps_per_relabel;
+            if (a.mode == GS_MODE_FIXED_SWEEPS) {
+                st.nrounds = min(st.nrounds, a.fixed_sweeps - st.rounds_total);
+                if (st.nrounds <= 0) {
+                    st.phase = PH_DONE;
+                    break;
+                }
+            }
+            st.round = 0;
+            st.sweep_depth = 0;
+            st.prev1 = st.prev2 = 1ll << 40;
+            st.phase = PH_SWEEP;
+            break;
+        }
+        case PH_SWEEP: {
+            const long long worked = v[0];
+            st.rounds_total++;
+            st.round++;
+            st.sweep_depth += step_depth(worked);
+            st.visits_sweep_total += worked;
+            const bool stalled = st.tail && st.round >= 3 && worked * 10 > st.prev2 * 9 &&
+                                 st.sweep_depth > st.last_relabel_depth;
+            st.prev2 = st.prev1;
+            st.prev1 = worked;
+            if (worked == 0 || stalled || st.round >= st.nrounds) {
+                if (a.mode == GS_MODE_FIXED_SWEEPS && st.rounds_total >= a.fixed_sweeps)
+                    st.phase = PH_DONE;
+                else
+                    start_relabel(st, a);
+            }
+            break;
+        }
+        case PH_LABELS:
+            st.active = v[0];      // sink capacity left
+            if (v[1]) st.status = GS_ERR_LABELS;
+            st.phase = PH_DONE;
+            break;
+        default:
+            break;
+    }
+}
+
+// Labels of one tile's sites and the tile's remaining sink capacity.
+__device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
+    const Geom &g = a.g;
+    const TileGeom &t = a.t;
+    const TileOrigin o = tile_origin(t, tile);
+    unsigned long long deficit = 0;
+    int b = 0;
+    for (int sidx = threadIdx.x; sidx < t.TW * t.TH; sidx += blockDim.x) {
+        const int wl = sidx % t.TW, yl = sidx / t.TW;
+        const int W = o.W0 + wl, y = o.y0 + yl;
+        if (W >= g.ng || y >= g.h) continue;
+        int64_t i = (int64_t)y * g.SY + W;
+        int lab = 0, prev = 1;
+        for (int j = 0; j < g.K; j++, i += g.P) {
+            const int32_t h = ld(&a.hgt[i]);
+            const int in = a.dir == 1 ? (h < kInfH) : (h >= kInfH);
+            b |= in && !prev;
+            lab += in;
+            prev = in;
+            const int32_t e = ld(&a.s.ex[i]);
+            if (e < 0) deficit += (unsigned long long)(-(int64_t)e);
+        }
+        a.labels[(int64_t)y * g.ng + W] = lab;
+    }
+    bad = __syncthreads_or(b);
+    return block_sum((long long)deficit);
+}
 
 template <int NPT>
-__global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
+__global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant__ BatchArgs B) {
     extern __shared__ int32_t smem[];
-    const TileSmem m = tile_smem(smem, a.t.PN);
-    Ctrl *ctrl = a.ctrl;
-    const int T = a.t.T;
-    long long relabels = 0, rounds = 0, passes = 0, visits = 0, sweep_visits = 0;
-    long long my_sweep_visits = 0;
-    const unsigned long long t_start = now_ns();
-    long long relabel_ns_local = 0;
-    unsigned long long t_relabel = 0, t_sweep = 0;
-    long long active = 0;
-    int converged = 0, overflow = 0, full = 0;
-    __shared__ int s_work;
-    for (long long outer = 0;; outer++) {
-        if (a.mode == GS_MODE_EXACT && outer >= a.max_iters) break;
-        // ---- global relabel: first pass (masks, heights reset, in-tile distances)
-        unsigned long long t0 = now_ns();
-        long long cnt = 0;
-        for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
-            cnt += relabel_init_tile<NPT>(a, m, tile);
-            visits++;
-            if (threadIdx.x == 0) {
-                __stcg(&a.tile_dirty[tile], 0);
-                __stcg(&a.tile_dirty[T + tile], 0);
-                __stcg(&a.tile_act[T + tile], 0);
-            }
-        }
-        active = grid_sync_sum(ctrl, threadIdx.x == 0 ? cnt : 0);
-        passes++;
-        if (aborted(ctrl)) break;
-        // ---- later passes: every tile once, then only tiles whose halo changed.
-        // An intermediate relabel stops after relabel_passes passes (heights of
-        // nodes not reached stay infinite until the next relabel); the relabel
-        // that can end the solve runs to its fixed point, which is exact.
-        int conv = 0;
-        for (int pass = 1;; pass++) {
-            int changed = 0;
-            long long delta = 0;
-            int32_t *dcur = a.tile_dirty + (pass & 1) * T;
-            int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
-            for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+    __shared__ PairState S[kMaxPairs];
+    __shared__ int s_work, s_all_done;
+    for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
+        PairState st;
+        memset(&st, 0, sizeof(st));
+        st.status = GS_OK;
+        start_relabel(st, B.pair[p]);
+        S[p] = st;
+    }
+    __syncthreads();
+    for (long long step = 0;; step++) {
+        long long *red = B.red + (step % 3) * B.n * 4;
+        for (int gt = blockIdx.x; gt < B.T_total; gt += gridDim.x) {
+            const int pr = pair_of(B, gt);
+            const int tile = gt - B.tile_off[pr];
+            const SolveArgs &a = B.pair[pr];
+            const int phase = S[pr].phase;
+            if (phase == PH_DONE) continue;
+            const TileSmem m = tile_smem(smem, a.t.PN);
+            const int T = a.t.T;
+            long long va = 0, vb = 0, vc = 0;
+            int ovf = 0;
+            if (phase == PH_INIT) {
+                va = relabel_init_tile<NPT>(a, m, tile);
+                vc = 1;
+                if (threadIdx.x == 0) {
+                    __stcg(&a.tile_dirty[tile], 0);
+                    __stcg(&a.tile_dirty[T + tile], 0);
+                    __stcg(&a.tile_act[T + tile], 0);
+                }
+            } else if (phase == PH_PASS) {
+                const int pass = S[pr].pass;
+                int32_t *dcur = a.tile_dirty + (pass & 1) * T;
+                int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
                 if (pass > 1) {
                     __syncthreads();
                     if (threadIdx.x == 0) s_work = ld(&dcur[tile]);
@@ -805,200 +991,78 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_solve_tiled(SolveArgs a) {
                     if (!s_work) continue;
                     if (threadIdx.x == 0) __stcg(&dcur[tile], 0);
                 }
-                delta += relabel_pass_tile<NPT>(a, m, tile, changed, dnext);
-                visits++;
-            }
-            const Sum2 r = grid_sync_sum2(ctrl, threadIdx.x == 0 ? delta : 0,
-                                          threadIdx.x == 0 ? changed : 0);
-            passes++;
-            active += r.a;
-            if (aborted(ctrl)) break;
-            if (r.b == 0) {
-                conv = 1;
-                break;
-            }
-            if (!full && pass >= a.relabel_passes) break;
-        }
-        // per-relabel log in the (otherwise idle during the solve) label-mark
-        // buffer: passes | converged << 32, active nodes, tile visits, elapsed ns
-        if (blockIdx.x == 0 && threadIdx.x == 0 && relabels < 256) {
-            long long *log = (long long *)a.log;
-            log[4 * relabels + 0] = passes | ((long long)conv << 32);
-            log[4 * relabels + 1] = active;
-            log[4 * relabels + 2] = sweep_visits;
-            log[4 * relabels + 3] = (long long)(now_ns() - t0);
-        }
-        // the relabel's duration as block 0 saw it, shared through the next barrier sum
-        relabel_ns_local = (long long)(now_ns() - t0);
-        relabels++;
-        t_relabel += now_ns() - t0;
-        if (aborted(ctrl)) break;
-        if (active == 0) {
-            if (conv) {
-                converged = 1;
-                break;
-            }
-            full = 1;          // nothing active within reach: decide with an exact relabel
-            continue;
-        }
-        full = 0;
-        // ---- sweep rounds over tiles with work.  While many nodes are active a
-        // relabel follows every sweeps_per_relabel rounds; in the tail (few
-        // active nodes, cheap rounds) up to 8x as many; rounds stop early once
-        // no tile has work.
-        const bool tail = active * 64 <= (long long)a.g.N;
-        long long n = tail ? 64ll * a.sweeps_per_relabel : a.sweeps_per_relabel;
-        const long long last_relabel_ns =
-            grid_sync_sum(ctrl, (blockIdx.x == 0 && threadIdx.x == 0) ? relabel_ns_local : 0);
-        const int iters = tail ? a.tail_iters : a.local_iters;
-        if (a.mode == GS_MODE_FIXED_SWEEPS) {
-            n = min(n, a.fixed_sweeps - rounds);
-            if (n <= 0) break;
-        }
-        t0 = now_ns();
-        long long prev1_worked = 1ll << 40, prev2_worked = 1ll << 40;
-        for (long long r = 0; r < n; r++) {
-            const int cur = (int)(r & 1);
-            long long worked = 0;
-            for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
+                int ch = 0;
+                va = relabel_pass_tile<NPT>(a, m, tile, ch, dnext);
+                vb = ch;
+                vc = 1;
+            } else if (phase == PH_SWEEP) {
+                const long long r = S[pr].round;
+                const int cur = (int)(r & 1);
                 __syncthreads();
                 if (threadIdx.x == 0)
                     s_work = r == 0 ? (ld(&a.tile_cnt[tile]) > 0) : ld(&a.tile_act[cur * T + tile]);
                 __syncthreads();
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
-                if (s_work) {
-                    sweep_tile<NPT>(a, m, tile, cur, iters, overflow);
-                    worked++;
-                    my_sweep_visits++;
-                }
-            }
-            // block 0's clock rides along the grid sum so every block takes the same
-            // decision: in the tail, sweep on until the rounds have cost as much as
-            // the last relabel and the number of tiles with work stopped falling
-            // (the excess left is circling on stale heights)
-            const Sum2 rs = grid_sync_sum2(
-                ctrl, threadIdx.x == 0 ? worked : 0,
-                (blockIdx.x == 0 && threadIdx.x == 0) ? (long long)(now_ns() - t0) : 0);
-            const long long tot_worked = rs.a;
-            const bool stalled = tail && r >= 2 && tot_worked * 10 > prev2_worked * 9 &&
-                                 rs.b > last_relabel_ns;
-            prev2_worked = prev1_worked;
-            prev1_worked = tot_worked;
-            if (blockIdx.x == 0 && threadIdx.x == 0 && rounds < 4096) {
-                // per-round log after the per-relabel log: tiles worked, end time
-                long long *log = (long long *)a.log + 1024;
-                log[2 * rounds + 0] = tot_worked | ((long long)relabels << 32);
-                log[2 * rounds + 1] = (long long)(now_ns() - t_start);
-            }
-            rounds++;
-            sweep_visits += tot_worked;
-            if (aborted(ctrl) || tot_worked == 0 || stalled) break;
-        }
-        t_sweep += now_ns() - t0;
-        if (aborted(ctrl)) break;
-    }
-    if (__syncthreads_or(overflow) && threadIdx.x == 0)
-        atomicCAS(&ctrl->status, GS_OK, GS_ERR_OVERFLOW);
-    if (threadIdx.x == 0) {
-        atomicAdd((unsigned long long *)&ctrl->visits_relabel, (unsigned long long)visits);
-        atomicAdd((unsigned long long *)&ctrl->visits_sweep, (unsigned long long)my_sweep_visits);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctrl->stats[0] = relabels;
-        ctrl->stats[1] = rounds;
-        ctrl->stats[2] = passes;
-        ctrl->stats[4] = active;
-        ctrl->stats[5] = (long long)t_sweep;
-        ctrl->stats[6] = (long long)t_relabel;
-        ctrl->converged = converged;
-        if (aborted(ctrl)) atomicCAS(&ctrl->status, GS_OK, GS_ERR_TIMEOUT);
-        else if (!converged && a.mode == GS_MODE_EXACT) atomicCAS(&ctrl->status, GS_OK, GS_ERR_TIMEOUT);
-    }
-}
-
-// ------------------------------------------------------------ labels ---
-
-// Reads the cut of the solved state back as labels, in one cooperative launch.
-// Exact mode: S_min = nodes reachable from positive excess over residual
-// arcs (dir 1, sources = excess nodes); a site's label is the number of its
-// chain nodes in S_min.  Fixed-sweep mode: the source side is the set of nodes
-// that cannot reach sink capacity (dir 0, exact distances, label = number of
-// chain nodes at infinite distance).  Both searches run to their fixed point.
-// The flow value is the sink capacity used: initial minus remaining deficit.
-template <int NPT>
-__global__ void __launch_bounds__(kTileThreads, 1)
-    k_extract_tiled(SolveArgs a, int32_t *labels, int64_t *flow, int32_t *status) {
-    extern __shared__ int32_t smem[];
-    const TileSmem m = tile_smem(smem, a.t.PN);
-    Ctrl *ctrl = a.ctrl;
-    const Geom &g = a.g;
-    const TileGeom &t = a.t;
-    const int T = t.T;
-    __shared__ int s_work;
-    long long passes = 1;
-    for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
-        relabel_init_tile<NPT>(a, m, tile);
-        if (threadIdx.x == 0) {
-            __stcg(&a.tile_dirty[tile], 0);
-            __stcg(&a.tile_dirty[T + tile], 0);
-        }
-    }
-    grid_sync_sum(ctrl, 0);
-    for (int pass = 1; !aborted(ctrl); pass++) {
-        int changed = 0;
-        int32_t *dcur = a.tile_dirty + (pass & 1) * T;
-        int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
-        for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
-            if (pass > 1) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_work = ld(&dcur[tile]);
-                __syncthreads();
                 if (!s_work) continue;
-                if (threadIdx.x == 0) __stcg(&dcur[tile], 0);
+                sweep_tile<NPT>(a, m, tile, cur, S[pr].tail ? a.tail_iters : a.local_iters, ovf);
+                ovf = __syncthreads_or(ovf);
+                va = 1;
+            } else {   // PH_LABELS
+                int bad = 0;
+                va = labels_tile(a, tile, bad);
+                vb = bad;
             }
-            relabel_pass_tile<NPT>(a, m, tile, changed, dnext);
-        }
-        const Sum2 r = grid_sync_sum2(ctrl, 0, threadIdx.x == 0 ? changed : 0);
-        passes++;
-        if (r.b == 0) break;
-    }
-    // labels of the tiles' sites and the sink capacity left
-    unsigned long long deficit = 0;
-    int bad = 0;
-    for (int tile = blockIdx.x; tile < T; tile += gridDim.x) {
-        const TileOrigin o = tile_origin(t, tile);
-        for (int sidx = threadIdx.x; sidx < t.TW * t.TH; sidx += blockDim.x) {
-            const int wl = sidx % t.TW, yl = sidx / t.TW;
-            const int W = o.W0 + wl, y = o.y0 + yl;
-            if (W >= g.ng || y >= g.h) continue;
-            int64_t i = (int64_t)y * g.SY + W;
-            int lab = 0, prev = 1;
-            for (int j = 0; j < g.K; j++, i += g.P) {
-                const int32_t h = ld(&a.hgt[i]);
-                const int in = a.dir == 1 ? (h < kInfH) : (h >= kInfH);
-                bad |= in && !prev;
-                lab += in;
-                prev = in;
-                const int32_t e = ld(&a.s.ex[i]);
-                if (e < 0) deficit += (unsigned long long)(-(int64_t)e);
+            if (threadIdx.x == 0) {
+                long long *rp = red + pr * 4;
+                if (va) atomicAdd((unsigned long long *)&rp[0], (unsigned long long)va);
+                if (vb) atomicAdd((unsigned long long *)&rp[1], (unsigned long long)vb);
+                if (vc) atomicAdd((unsigned long long *)&rp[2], (unsigned long long)vc);
+                if (ovf) atomicAdd((unsigned long long *)&rp[3], 1ull);
             }
-            labels[(int64_t)y * g.ng + W] = lab;
+        }
+        // the sums of step + 1 start from zero (their slot was last read two
+        // barriers ago)
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < B.n * 4; i += blockDim.x)
+                B.red[((step + 1) % 3) * B.n * 4 + i] = 0;
+        grid_sync_sum(B.bar, 0);
+        if (aborted(B.bar)) break;
+        int done = 1;
+        for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
+            long long v[4];
+            for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&red[p * 4 + k];
+            advance(S[p], B.pair[p], v, B.extract);
+            done &= S[p].phase == PH_DONE;
+        }
+        if (__syncthreads_and(done)) break;
+    }
+    // per-pair results (block 0): statistics, flow value, status
+    if (blockIdx.x == 0) {
+        const bool ab = aborted(B.bar);
+        for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
+            const SolveArgs &a = B.pair[p];
+            const PairState &st = S[p];
+            int status = st.status;
+            if (ab && status == GS_OK) status = GS_ERR_TIMEOUT;
+            if (!B.extract) {
+                Ctrl *c = a.ctrl;
+                c->stats[0] = st.relabels;
+                c->stats[1] = st.rounds_total;
+                c->stats[2] = st.passes;
+                c->stats[4] = st.active;
+                c->stats[5] = 0;
+                c->stats[6] = 0;
+                c->stats[7] = 1;
+                c->visits_sweep = st.visits_sweep_total;
+                c->visits_relabel = st.visits_relabel_total;
+                c->converged = st.phase == PH_DONE && status == GS_OK;
+            } else {
+                a.ctrl->stats[3] = st.passes;
+                *a.flow = (int64_t)a.s.hdr->init_deficit - st.active;
+            }
+            if (status != GS_OK) atomicCAS(a.status, GS_OK, status);
         }
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_LABELS);
-    const long long tot = block_sum((long long)deficit);
-    const long long all = grid_sync_sum(ctrl, threadIdx.x == 0 ? tot : 0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *flow = (int64_t)a.s.hdr->init_deficit - all;
-        ctrl->stats[3] = passes;
-        if (aborted(ctrl)) atomicCAS(status, GS_OK, GS_ERR_TIMEOUT);
-    }
-}
-
-// copy the solve's device status into the caller's word unless it holds an error
-__global__ void k_publish_status(Ctrl *ctrl, int32_t *status, int launches) {
-    if (*status == GS_OK && ctrl->status != GS_OK) *status = ctrl->status;
-    ctrl->stats[7] = launches;
 }
 
 // ------------------------------------------------------------ host side ---
@@ -1046,8 +1110,10 @@ size_t tiled_work_extra(const Geom &g) {
     return round_up(g.N * sizeof(uint16_t), 256) + round_up(5 * (int64_t)t.T * sizeof(int32_t), 256);
 }
 
+// Per-pair arguments from the pair's geometry, state and workspace.
 static int setup_args(const Geom &g, const State &s, const Work &w, SolveArgs &a, int &npt,
                       size_t &smem) {
+    memset(&a, 0, sizeof(a));
     a.g = g;
     a.s = s;
     if (!pick_tile(g, a.t, npt, smem)) return GS_ERR_INVAL;
@@ -1056,14 +1122,27 @@ static int setup_args(const Geom &g, const State &s, const Work &w, SolveArgs &a
     a.tile_act = (int32_t *)(extra + round_up(g.N * sizeof(uint16_t), 256));
     a.tile_dirty = a.tile_act + 2 * a.t.T;
     a.tile_cnt = a.tile_act + 4 * a.t.T;
-    a.log = w.mark;
     a.ctrl = w.ctrl;
     return GS_OK;
 }
 
-// Cooperative launch of kern with the whole grid resident.
-template <class... Args>
-static int launch_coop(void (*kern)(Args...), size_t smem, int T, cudaStream_t st, void **args) {
+static void solve_fields(SolveArgs &a, const gs_solve_opts *o) {
+    a.hgt = a.s.ht;
+    a.dir = 0;
+    a.mode = o->mode;
+    a.sweeps_per_relabel = o->sweeps_per_relabel;
+    a.local_iters = o->local_iters > 0 ? o->local_iters : 8;
+    a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 4;
+    a.tail_iters = o->tail_iters > 0 ? o->tail_iters : 4 * a.local_iters;
+    a.fixed_sweeps = o->fixed_sweeps;
+    a.max_iters = o->max_iters;
+}
+
+// Cooperative launch of the batch kernel with the whole grid resident.  The
+// launch goes through cudaLaunchKernelEx with the cooperative attribute, so a
+// caller may capture it in a CUDA graph.
+static int launch_batch(const BatchArgs &B, int npt, size_t smem, cudaStream_t st) {
+    void (*kern)(const BatchArgs) = npt == 4 ? k_batch<4> : k_batch<8>;
     int dev = 0;
     GS_CUDA_TRY(cudaGetDevice(&dev));
     int sms = 0, coop = 0;
@@ -1074,56 +1153,79 @@ static int launch_coop(void (*kern)(Args...), size_t smem, int T, cudaStream_t s
     int per_sm = 0;
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem));
     if (per_sm < 1) return GS_ERR_INVAL;
-    const int grid = std::min(per_sm * sms, T);
-    GS_CUDA_TRY(cudaLaunchCooperativeKernel((void *)kern, grid, kTileThreads, args, smem, st));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::min(per_sm * sms, B.T_total));
+    cfg.blockDim = dim3(kTileThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, B));
     count_launches(1);
     return GS_OK;
 }
 
+// Control words of a batch launch: the barrier block, then the per-step sums.
+constexpr size_t kBatchCtrlBytes = 256 + 3 * kMaxPairs * 4 * sizeof(long long);
+
+static int run_batch(BatchArgs &B, int npt, size_t smem, void *ctrl_mem, cudaStream_t st) {
+    B.bar = (Ctrl *)ctrl_mem;
+    B.red = (long long *)((char *)ctrl_mem + 256);
+    int total = 0;
+    for (int p = 0; p < B.n; p++) {
+        B.tile_off[p] = total;
+        total += B.pair[p].t.T;
+    }
+    B.tile_off[B.n] = total;
+    B.T_total = total;
+    GS_CUDA_TRY(cudaMemsetAsync(ctrl_mem, 0, 256 + 3 * (size_t)B.n * 4 * sizeof(long long), st));
+    return launch_batch(B, npt, smem, st);
+}
+
+size_t batch_ctrl_bytes() { return kBatchCtrlBytes; }
+
 int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
                 int32_t *status, cudaStream_t st) {
-    SolveArgs a;
+    static BatchArgs B;   // host staging of the kernel argument (copied at launch)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    memset(&B, 0, sizeof(B));
+    B.n = 1;
+    B.extract = 0;
     int npt;
     size_t smem;
-    int rc = setup_args(g, s, w, a, npt, smem);
+    int rc = setup_args(g, s, w, B.pair[0], npt, smem);
     if (rc) return rc;
-    a.hgt = s.ht;
-    a.dir = 0;
-    a.mode = o->mode;
-    a.sweeps_per_relabel = o->sweeps_per_relabel;
-    a.local_iters = o->local_iters > 0 ? o->local_iters : 8;
-    a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 4;
-    a.tail_iters = o->tail_iters > 0 ? o->tail_iters : 4 * a.local_iters;
-    a.fixed_sweeps = o->fixed_sweeps;
-    a.max_iters = o->max_iters;
+    solve_fields(B.pair[0], o);
+    B.pair[0].status = status;
     GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
-    void *args[] = {&a};
-    rc = npt == 4 ? launch_coop(k_solve_tiled<4>, smem, a.t.T, st, args)
-                  : launch_coop(k_solve_tiled<8>, smem, a.t.T, st, args);
-    if (rc) return rc;
-    k_publish_status<<<1, 1, 0, st>>>(w.ctrl, status, 2);
-    count_launches(1);
-    GS_CUDA_TRY(cudaGetLastError());
-    return GS_OK;
+    return run_batch(B, npt, smem, (char *)w.ctrl + 256, st);
 }
 
 int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
                   int32_t *labels, int64_t *flow, int32_t *status, cudaStream_t st) {
-    SolveArgs a;
+    static BatchArgs B;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    memset(&B, 0, sizeof(B));
+    B.n = 1;
+    B.extract = 1;
     int npt;
     size_t smem;
-    int rc = setup_args(g, s, w, a, npt, smem);
+    int rc = setup_args(g, s, w, B.pair[0], npt, smem);
     if (rc) return rc;
+    SolveArgs &a = B.pair[0];
     a.hgt = w.mark;
     a.dir = o->mode == GS_MODE_EXACT ? 1 : 0;
-    // control words only: keep the solve's statistics, reset the barrier
-    GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, offsetof(Ctrl, stats), st));
-    void *args[] = {&a, &labels, &flow, &status};
-    rc = npt == 4 ? launch_coop(k_extract_tiled<4>, smem, a.t.T, st, args)
-                  : launch_coop(k_extract_tiled<8>, smem, a.t.T, st, args);
-    if (rc) return rc;
-    GS_CUDA_TRY(cudaGetLastError());
-    return GS_OK;
+    a.mode = GS_MODE_EXACT;
+    a.max_iters = 1;
+    a.labels = labels;
+    a.flow = flow;
+    a.status = status;
+    return run_batch(B, npt, smem, (char *)w.ctrl + 256, st);
 }
 
 }  // namespace gs
@@ -1140,4 +1242,68 @@ extern "C" int gs_tile_info(const gs_params *p, int32_t *out) {
     out[2] = t.T;
     out[3] = (int32_t)smem;
     return GS_OK;
+}
+
+// ------------------------------------------------------------ batched ABI ---
+
+extern "C" size_t gs_batch_workspace_bytes(int32_t n) {
+    if (n < 1 || n > gs::kMaxPairs) return 0;
+    return gs::kBatchCtrlBytes;
+}
+
+extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batch_ws, void *stream) {
+    using namespace gs;
+    if (!descs || n < 1 || n > kMaxPairs || !batch_ws || ((uintptr_t)batch_ws & 255))
+        return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    static BatchArgs B, E;   // host staging of the kernel arguments (copied at launch)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    memset(&B, 0, sizeof(B));
+    memset(&E, 0, sizeof(E));
+    B.n = E.n = n;
+    B.extract = 0;
+    E.extract = 1;
+    int npt_max = 4;
+    size_t smem_max = 0;
+    for (int i = 0; i < n; i++) {
+        const gs_pair_desc &d = descs[i];
+        Geom g;
+        if (make_geom(&d.p, &g) != GS_OK || !d.L || !d.R || !d.cost || !d.graph || !d.workspace ||
+            !d.labels || !d.flow || !d.status)
+            return GS_ERR_INVAL;
+        if (d.o.engine != GS_ENGINE_TILED || d.o.sweeps_per_relabel < 1 || d.o.max_iters < 1 ||
+            d.o.reserved != 0 || ((uintptr_t)d.graph & 255) || ((uintptr_t)d.workspace & 255))
+            return GS_ERR_INVAL;
+        const State s = state_view(d.graph, g);
+        const Work w = work_view(d.workspace, g);
+        int npt;
+        size_t smem;
+        if (setup_args(g, s, w, B.pair[i], npt, smem) != GS_OK) return GS_ERR_INVAL;
+        solve_fields(B.pair[i], &d.o);
+        B.pair[i].status = d.status;
+        E.pair[i] = B.pair[i];
+        SolveArgs &x = E.pair[i];
+        x.hgt = w.mark;
+        x.dir = d.o.mode == GS_MODE_EXACT ? 1 : 0;
+        x.mode = GS_MODE_EXACT;
+        x.max_iters = 1;
+        x.labels = d.labels;
+        x.flow = d.flow;
+        npt_max = std::max(npt_max, npt);
+        smem_max = std::max(smem_max, smem);
+    }
+    // per pair: data term and graph (small launches), then one launch for all
+    // solves and one for all label extractions
+    for (int i = 0; i < n; i++) {
+        const gs_pair_desc &d = descs[i];
+        int rc = gs_stereo_cost_volume(d.L, d.R, d.p.w, &d.p, d.cost, stream);
+        if (rc) return rc;
+        rc = gs_build_graph(d.cost, &d.p, d.graph, d.status, stream);
+        if (rc) return rc;
+        GS_CUDA_TRY(cudaMemsetAsync(B.pair[i].ctrl, 0, sizeof(Ctrl), st));
+    }
+    int rc = run_batch(B, npt_max, smem_max, batch_ws, st);
+    if (rc) return rc;
+    return run_batch(E, npt_max, smem_max, batch_ws, st);
 }

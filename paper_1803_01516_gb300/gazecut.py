@@ -31,7 +31,7 @@ EXPORTS = [
     "gs_extract_labels", "gs_energy", "gs_solve_stats", "gs_kernel_launches",
     "gs_noalloc_scratch_bytes", "gs_maxflow_solve_noalloc", "gs_tile_info",
     "gs_stereo_cost_volume_f32", "gs_energy_backward", "gs_cost_volume_f32_backward",
-    "gs_cost_add_at_labels",
+    "gs_cost_add_at_labels", "gs_batch_workspace_bytes", "gs_solve_batched",
 ]
 
 
@@ -47,6 +47,12 @@ class GsSolveOpts(ctypes.Structure):
                 ("max_iters", ctypes.c_int64), ("local_iters", ctypes.c_int32),
                 ("relabel_passes", ctypes.c_int32), ("tail_iters", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class GsPairDesc(ctypes.Structure):
+    _fields_ = [("p", GsParams), ("o", GsSolveOpts), ("L", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("cost", ctypes.c_void_p), ("graph", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("flow", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
 @dataclass
@@ -125,6 +131,8 @@ def lib():
             "gs_energy_backward": ([P, pp, F, P, P, P], ctypes.c_int),
             "gs_cost_volume_f32_backward": ([P, P, I32, pp, F, F, F, P, P, P], ctypes.c_int),
             "gs_cost_add_at_labels": ([P, P, pp, I32, P], ctypes.c_int),
+            "gs_batch_workspace_bytes": ([I32], SZ),
+            "gs_solve_batched": ([P, I32, P, P], ctypes.c_int),
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -331,3 +339,39 @@ def solve_costs(cost: torch.Tensor, p: Params, o: SolveOpts | None = None,
     gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status, stream)
     gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status, stream)
     return buf.labels, buf.flow, buf.status
+
+
+# ------------------------------------------------------------- batches ---
+
+class Batch:
+    """Device buffers for a batch of pairs of uneven sizes (one Buffers each)."""
+
+    def __init__(self, params: list, opts: list, device="cuda"):
+        if not 1 <= len(params) <= 64:
+            raise ValueError("a batch holds 1 to 64 pairs")
+        self.params, self.opts = params, opts
+        self.bufs = [Buffers(p, o, device=device) for p, o in zip(params, opts)]
+        self.ws = torch.empty(lib().gs_batch_workspace_bytes(len(params)), dtype=torch.uint8,
+                              device=device)
+        self._descs = None
+
+    def descs(self, Ls, Rs):
+        n = len(self.params)
+        arr = (GsPairDesc * n)()
+        for i, (p, o, b, L, R) in enumerate(zip(self.params, self.opts, self.bufs, Ls, Rs)):
+            if L.shape != (p.h, p.w) or R.shape != (p.h, p.w):
+                raise ValueError(f"pair {i}: images must be [h, w]")
+            arr[i] = GsPairDesc(p.c(), o.c(), _dev(L, torch.uint8, "L").value,
+                                _dev(R, torch.uint8, "R").value, b.cost.data_ptr(),
+                                b.graph.data_ptr(), b.work.data_ptr(), b.labels.data_ptr(),
+                                b.flow.data_ptr(), b.status.data_ptr())
+        self._descs = arr       # keep alive
+        return arr
+
+
+def gs_solve_batched(batch: Batch, Ls, Rs, stream=None):
+    """All pairs of the batch through the whole path (two persistent launches)."""
+    arr = batch.descs(Ls, Rs)
+    rc = lib().gs_solve_batched(ctypes.cast(arr, ctypes.c_void_p), len(arr),
+                                _dev(batch.ws, torch.uint8, "batch workspace"), _stream(stream))
+    _check(rc, "gs_solve_batched")

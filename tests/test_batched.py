@@ -1,0 +1,106 @@
+"""Batched solve: uneven pairs in one persistent launch, each bit-exact against
+the oracle and against the single-pair path; CUDA-graph capture and replay."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01516_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1803_01516_gb300 import build
+    build.build()
+    from paper_1803_01516_gb300 import gazecut
+    return gazecut
+
+
+def _uneven_batch(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        D = int(rng.integers(4, 41))
+        w = int(rng.integers(2 * (D - 1) + 20, 2 * (D - 1) + 140))
+        h = int(rng.integers(9, 60))
+        wl = synth.Workload(f"b{i}", w, h, D, tau=30, lam=int(rng.integers(2, 12)), sigma=2.0,
+                            scene="layers", n_layers=3, n_slanted=1,
+                            max_disp=min(2 * (D - 1), 20), seed_base=50 + seed)
+        L, R, _ = synth.make_pair(wl, i)
+        out.append((wl, L, R, int(rng.integers(0, 2))))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_batched_matches_oracle_and_single(gc, seed):
+    pairs = _uneven_batch(7, seed)
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                        vertical_inhibit=vi) for wl, _, _, vi in pairs]
+    opts = [gc.SolveOpts() for _ in pairs]
+    batch = gc.Batch(params, opts)
+    Ls = [torch.from_numpy(L).cuda() for _, L, _, _ in pairs]
+    Rs = [torch.from_numpy(R).cuda() for _, _, R, _ in pairs]
+    gc.gs_solve_batched(batch, Ls, Rs)
+    torch.cuda.synchronize()
+    for (wl, L, R, vi), p, b, Ld, Rd in zip(pairs, params, batch.bufs, Ls, Rs):
+        C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+        ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
+        assert int(b.status.item()) == gc.GS_OK
+        assert int(b.flow.item()) == ref["flow"]
+        assert np.array_equal(b.labels.cpu().numpy(), ref["labels"])
+        lab, flow, status = gc.solve_pair(Ld, Rd, p)
+        assert int(flow.item()) == ref["flow"] and np.array_equal(lab.cpu().numpy(), ref["labels"])
+
+
+def test_batched_fixed_sweeps_and_mixed_options(gc):
+    pairs = _uneven_batch(4, 3)
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit)
+              for wl, _, _, _ in pairs]
+    opts = [gc.SolveOpts(), gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=2),
+            gc.SolveOpts(sweeps_per_relabel=2, local_iters=4), gc.SolveOpts(relabel_passes=16)]
+    batch = gc.Batch(params, opts)
+    gc.gs_solve_batched(batch, [torch.from_numpy(L).cuda() for _, L, _, _ in pairs],
+                        [torch.from_numpy(R).cuda() for _, _, R, _ in pairs])
+    torch.cuda.synchronize()
+    for (wl, L, R, _), o, b in zip(pairs, opts, batch.bufs):
+        C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+        ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+        assert int(b.status.item()) == gc.GS_OK
+        if o.mode == gc.GS_MODE_EXACT:
+            assert int(b.flow.item()) == ref["flow"]
+            assert np.array_equal(b.labels.cpu().numpy(), ref["labels"])
+        else:
+            E = oracle.energy(C, b.labels.cpu().numpy(), wl.lam, wl.inhibit, 1)
+            assert int(b.flow.item()) <= ref["flow"] <= E
+
+
+def test_batched_call_captured_in_a_cuda_graph(gc):
+    pairs = _uneven_batch(5, 4)
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit)
+              for wl, _, _, _ in pairs]
+    opts = [gc.SolveOpts() for _ in pairs]
+    batch = gc.Batch(params, opts)
+    Ls = [torch.from_numpy(L).cuda() for _, L, _, _ in pairs]
+    Rs = [torch.from_numpy(R).cuda() for _, _, R, _ in pairs]
+    gc.gs_solve_batched(batch, Ls, Rs)          # first call outside capture (set-up)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            gc.gs_solve_batched(batch, Ls, Rs)
+    for b in batch.bufs:
+        b.flow.zero_()
+        b.labels.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for (wl, L, R, _), b in zip(pairs, batch.bufs):
+        C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+        ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+        assert int(b.status.item()) == gc.GS_OK
+        assert int(b.flow.item()) == ref["flow"]
+        assert np.array_equal(b.labels.cpu().numpy(), ref["labels"])
