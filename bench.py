@@ -17,6 +17,8 @@ Extra keys on the JSON line:
   cpu_baseline  the CPU oracle (Boykov-Kolmogorov) on the bench's distinct pairs,
                 whose results also check the timed GPU results (parity_vs_oracle)
   clocks        SM clocks and throttle reasons sampled during the timed steps
+  batched       64 uneven pairs in one batched call (pairs/s) vs one call per pair
+  differentiated  forward exact solve + backward, 16 pairs at 384x288x32
 
 --impl reference times the CPU oracle on the same workload (the reference arm).
 Multi-GPU (torchrun): replicas, each rank solves its own pairs; no collective
@@ -203,6 +205,89 @@ def run_reference(args):
     return 0
 
 
+def _batched(gc, dev, args, stream, flush):
+    """64 synthetic pairs of uneven size and depth range in one batched call
+    (two persistent launches) vs the same pairs solved one call at a time."""
+    import torch
+    from paper_1803_01516_gb300 import autotune
+    batch = synth.make_batch(args.batch_pairs)
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                        vertical_inhibit=1) for wl, _, _, _ in batch]
+    opts = [autotune.tuned_opts(p) for p in params]
+    B = gc.Batch(params, opts, device=dev)
+    Ls = [torch.from_numpy(L).to(dev) for _, L, _, _ in batch]
+    Rs = [torch.from_numpy(R).to(dev) for _, _, R, _ in batch]
+    gc.gs_solve_batched(B, Ls, Rs)                    # warm-up
+    torch.cuda.synchronize(dev)
+    times = []
+    for i in range(args.batch_steps):
+        flush.fill_(i & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gc.gs_solve_batched(B, Ls, Rs)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    ok = all(int(b.status.item()) == gc.GS_OK for b in B.bufs)
+    flows = [int(b.flow.item()) for b in B.bufs]
+    # the same pairs, one call each (same buffers, same options)
+    t_single = 0.0
+    for i, (p, o, buf) in enumerate(zip(params, opts, B.bufs)):
+        flush.fill_(i & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gc.solve_pair(Ls[i], Rs[i], p, o, buf)
+        b.record(stream)
+        b.synchronize()
+        t_single += a.elapsed_time(b)
+        ok &= int(buf.flow.item()) == flows[i]
+    nodes = sum(gc.gs_num_nodes(p) for p in params)
+    out = {"pairs": len(params), "nodes": nodes, "ms_per_batch": float(np.mean(times)),
+           "pairs_per_s": 1e3 * len(params) / float(np.mean(times)),
+           "single_call_loop_ms": t_single,
+           "single_call_pairs_per_s": 1e3 * len(params) / t_single,
+           "flows_match_single_calls": bool(ok),
+           "workload": "64 pairs, w~U[160,640], h~U[120,480], D~U[16,64], layered scenes"}
+    if not args.no_cpu_baseline:
+        import oracle
+        order = np.argsort([gc.gs_num_nodes(p) for p in params])[:2]
+        good = True
+        for k in order:
+            wl, L, R, _ = batch[k]
+            C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+            ref = oracle.solve(C, wl.lam, wl.inhibit, 1, "bk")
+            good &= flows[k] == ref["flow"] and bool(np.array_equal(
+                B.bufs[k].labels.cpu().numpy(), ref["labels"]))
+        out["parity_vs_oracle"] = {"pairs_checked": len(order), "equal": good}
+    return out
+
+
+def _differentiated(gc, dev, args, stream):
+    """Forward exact solve + backward on 16 pairs at 384x288 with 32 depth
+    numbers (learned FP32 data term, scale 256)."""
+    import torch
+    from paper_1803_01516_gb300 import learn
+    wl = synth.Workload("diff-384x288x32", 384, 288, 32, tau=30, lam=8, sigma=2.0, scene="layers",
+                        n_layers=5, n_slanted=2, max_disp=31, seed_base=5)
+    probs = []
+    for i in range(args.diff_pairs):
+        L, R, _ = synth.make_pair(wl, i)
+        p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=0, lam=0, inhibit=1023 * 256)
+        probs.append(learn.problem(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), p))
+    theta = torch.tensor([1.0, 1.0, 30.0, 8.0], dtype=torch.float64, requires_grad=True)
+    learn.min_energy(theta, probs[0]).backward()        # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for pr in probs:
+        theta.grad = None
+        learn.min_energy(theta, pr).backward()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"pairs": len(probs), "ms_per_pair_fwd_bwd": 1e3 * dt / len(probs),
+            "pairs_per_s": len(probs) / dt,
+            "workload": "384x288, 32 depth numbers, learned FP32 cost at scale 256"}
+
+
 def run(args):
     import torch
 
@@ -348,6 +433,9 @@ def run(args):
             ok_lab &= bool(np.array_equal(buf.labels.cpu().numpy(), ref["labels"]))
         parity = {"pairs": len(refs), "flow_equal": ok_flow, "labels_equal": ok_lab}
 
+    batched = None if args.no_batched or world > 1 else _batched(gc, dev, args, stream, flush)
+    diff = None if args.no_batched or world > 1 else _differentiated(gc, dev, args, stream)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": False,
@@ -368,6 +456,8 @@ def run(args):
                       "extract_labels": float(np.mean(extract_ms))},
         "cpu_baseline": cpu,
         "parity_vs_oracle": parity,
+        "batched": batched,
+        "differentiated": diff,
         "clocks": clk,
         "gpu_launches": int(launches),
         "solver": {k: float(np.mean([s[k] for s in stats])) for k in
@@ -391,6 +481,10 @@ def main():
     ap.add_argument("--local-iters", type=int, default=8)
     ap.add_argument("--relabel-passes", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--diff-pairs", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

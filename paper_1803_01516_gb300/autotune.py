@@ -1,0 +1,125 @@
+"""Autotuner for the solver schedule, per problem-size bucket, cached in JSON.
+
+The tile shape follows from the depth range (the library picks the squarest
+tile of whole depth chains that fits shared memory).  What is tuned here is
+the schedule: sweep rounds between global relabels, local push/relabel
+iterations per tile visit, and the pass cap of intermediate relabels.  A
+bucket is (depth numbers, log2 of the node count); its entry is measured on a
+seeded synthetic pair of that size (the same scene generator as the tests)
+with CUDA events, the best median over a few runs kept.
+
+The cache lives in $GAZECUT_TUNE_CACHE or ~/.cache/gazecut_gb300/autotune.json;
+buckets missing there fall back to ``tuned_defaults.json`` beside this module
+(entries measured on a GB300 with ``python -m paper_1803_01516_gb300.autotune``),
+then to the library defaults.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import torch
+
+from . import gazecut as gc
+from . import synth
+
+CANDIDATES = [(spr, li, rp) for spr in (4, 8, 16, 32) for li in (4, 8, 16) for rp in (4, 8, 16)]
+
+
+def cache_path() -> str:
+    return os.environ.get("GAZECUT_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "gazecut_gb300",
+                                       "autotune.json"))
+
+
+def bucket(p: gc.Params) -> str:
+    nodes = max(p.ng * p.h * (p.D - 1), 1)
+    return f"D{p.D}-n{int(round(math.log2(nodes)))}"
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(d: dict):
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
+    spr, li, rp = cfg
+    o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp)
+    buf = gc.Buffers(p, o)
+    ts = []
+    for L, R in pairs:
+        gc.gs_stereo_cost_volume(L, R, p, buf.cost)
+        for _ in range(reps):
+            gc.gs_build_graph(buf.cost, p, buf.graph, buf.status)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+            b.record()
+            b.synchronize()
+            if int(buf.status.item()) != gc.GS_OK:
+                return float("inf")
+            ts.append(a.elapsed_time(b))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def tune(p: gc.Params, n_pairs: int = 2, candidates=CANDIDATES, save: bool = True) -> dict:
+    """Measure every candidate schedule on synthetic pairs of p's size."""
+    wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
+                        scene="layers", n_layers=5, n_slanted=2,
+                        max_disp=min(2 * (p.D - 1), 40), seed_base=77)
+    pairs = []
+    for i in range(n_pairs):
+        L, R, _ = synth.make_pair(wl, i)
+        pairs.append((torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()))
+    results = {f"{c[0]},{c[1]},{c[2]}": _time_config(p, pairs, c) for c in candidates}
+    best = min(results, key=results.get)
+    entry = {"best": [int(x) for x in best.split(",")], "ms": results[best], "all_ms": results}
+    if save:
+        d = _load()
+        d[bucket(p)] = entry
+        _save(d)
+    return entry
+
+
+def _defaults() -> dict:
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "tuned_defaults.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpts:
+    """Solve options for p from the cache (library defaults when absent)."""
+    entry = _load().get(bucket(p)) or _defaults().get(bucket(p))
+    if entry is None and tune_if_missing:
+        entry = tune(p)
+    if entry is None:
+        return gc.SolveOpts(**kw)
+    spr, li, rp = entry["best"]
+    return gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, **kw)
+
+
+if __name__ == "__main__":
+    import sys
+    # tune the buckets given as w,h,D triples (default: the benchmark's sizes)
+    sizes = [tuple(int(x) for x in a.split(",")) for a in sys.argv[1:]] or [(384, 288, 16)]
+    for w, h, D in sizes:
+        p = gc.Params(w=w, h=h, D=D, tau=30, lam=10)
+        e = tune(p)
+        print(json.dumps({bucket(p): e}), flush=True)
