@@ -411,7 +411,7 @@ def run(args):
     # ----- roofline of the dominant kernel (the persistent solve) -----
     peak, peak_kind = _peaks()
     nodes = gc.gs_num_nodes(p)
-    ti = gc.gs_tile_info(p)
+    ti = gc.gs_tile_info(p, o)
     nodes_per_tile = nodes / ti["tiles"]
     sweep_visits = float(np.mean([s["sweep_visits"] for s in stats]))
     relabel_visits = float(np.mean([s["relabel_visits"] for s in stats]))

@@ -98,6 +98,10 @@ typedef struct gs_solve_opts {
                                     runs to its fixed point */
     int32_t tail_iters;          /* TILED: local iterations per tile visit once few nodes
                                     are active (0: 4 x local_iters) */
+    int32_t tile_w, tile_h;      /* TILED: sites per tile along W (4, 8, 16 or 32) and
+                                    rows per tile (1..8); 0, 0: chosen by the library.
+                                    A shape that does not fit shared memory is refused
+                                    (GS_ERR_INVAL). */
     int32_t reserved;            /* must be 0 */
 } gs_solve_opts;
 
@@ -248,9 +252,10 @@ GS_API size_t gs_batch_workspace_bytes(int32_t n);
 GS_API int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batch_workspace,
                             void *stream);
 
-/* Tile shape the TILED engine uses for these params: host int32[4] =
- * {sites per tile along W, rows per tile, number of tiles, shared bytes}. */
-GS_API int gs_tile_info(const gs_params *p, int32_t *out);
+/* Tile shape the TILED engine uses for these params and options: host
+ * int32[4] = {sites per tile along W, rows per tile, number of tiles, shared
+ * bytes}.  GS_ERR_INVAL if the requested shape does not fit. */
+GS_API int gs_tile_info(const gs_params *p, const gs_solve_opts *o, int32_t *out);
 
 /* Number of kernels this library has launched in this process so far. */
 GS_API int64_t gs_kernel_launches(void);

@@ -1,12 +1,11 @@
 """Autotuner for the solver schedule, per problem-size bucket, cached in JSON.
 
-The tile shape follows from the depth range (the library picks the squarest
-tile of whole depth chains that fits shared memory).  What is tuned here is
-the schedule: sweep rounds between global relabels, local push/relabel
-iterations per tile visit, and the pass cap of intermediate relabels.  A
-bucket is (depth numbers, log2 of the node count); its entry is measured on a
-seeded synthetic pair of that size (the same scene generator as the tests)
-with CUDA events, the best median over a few runs kept.
+What is tuned: the tile shape (sites per tile along W and y; every tile holds
+whole depth chains) and the schedule (sweep rounds between global relabels,
+local push/relabel iterations per tile visit, the pass cap of intermediate
+relabels).  A bucket is (depth numbers, log2 of the node count); its entry is
+measured on seeded synthetic pairs of that size (the same scene generator as
+the tests) with CUDA events, the best median over a few runs kept.
 
 The cache lives in $GAZECUT_TUNE_CACHE or ~/.cache/gazecut_gb300/autotune.json;
 buckets missing there fall back to ``tuned_defaults.json`` beside this module
@@ -24,7 +23,8 @@ import torch
 from . import gazecut as gc
 from . import synth
 
-CANDIDATES = [(spr, li, rp) for spr in (4, 8, 16, 32) for li in (4, 8, 16) for rp in (4, 8, 16)]
+SCHEDULES = [(spr, li, rp) for spr in (4, 8, 16, 32) for li in (4, 8, 16) for rp in (4, 8, 16)]
+SHAPES = [(16, 8), (8, 8), (16, 4), (32, 4), (8, 4), (16, 2), (8, 2), (4, 4)]
 
 
 def cache_path() -> str:
@@ -56,8 +56,13 @@ def _save(d: dict):
 
 
 def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
-    spr, li, rp = cfg
-    o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp)
+    spr, li, rp, tw, th = cfg
+    o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
+                     tile_h=th)
+    try:
+        gc.gs_tile_info(p, o)
+    except RuntimeError:
+        return float("inf")          # the shape does not fit this depth range
     buf = gc.Buffers(p, o)
     ts = []
     for L, R in pairs:
@@ -76,8 +81,9 @@ def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
     return ts[len(ts) // 2]
 
 
-def tune(p: gc.Params, n_pairs: int = 2, candidates=CANDIDATES, save: bool = True) -> dict:
-    """Measure every candidate schedule on synthetic pairs of p's size."""
+def tune(p: gc.Params, n_pairs: int = 2, save: bool = True) -> dict:
+    """Tile shape first (default schedule), then the schedule on the best shape,
+    each measured on synthetic pairs of p's size."""
     wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
                         scene="layers", n_layers=5, n_slanted=2,
                         max_disp=min(2 * (p.D - 1), 40), seed_base=77)
@@ -85,7 +91,14 @@ def tune(p: gc.Params, n_pairs: int = 2, candidates=CANDIDATES, save: bool = Tru
     for i in range(n_pairs):
         L, R, _ = synth.make_pair(wl, i)
         pairs.append((torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()))
-    results = {f"{c[0]},{c[1]},{c[2]}": _time_config(p, pairs, c) for c in candidates}
+    results = {}
+    for tw, th in SHAPES:
+        results[f"16,8,8,{tw},{th}"] = _time_config(p, pairs, (16, 8, 8, tw, th))
+    shape = [int(x) for x in min(results, key=results.get).split(",")][3:]
+    for spr, li, rp in SCHEDULES:
+        key = f"{spr},{li},{rp},{shape[0]},{shape[1]}"
+        if key not in results:
+            results[key] = _time_config(p, pairs, (spr, li, rp, *shape))
     best = min(results, key=results.get)
     entry = {"best": [int(x) for x in best.split(",")], "ms": results[best], "all_ms": results}
     if save:
@@ -111,8 +124,11 @@ def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpt
         entry = tune(p)
     if entry is None:
         return gc.SolveOpts(**kw)
-    spr, li, rp = entry["best"]
-    return gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, **kw)
+    best = entry["best"]
+    spr, li, rp = best[:3]
+    tw, th = (best[3], best[4]) if len(best) == 5 else (0, 0)
+    return gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
+                        tile_h=th, **kw)
 
 
 if __name__ == "__main__":

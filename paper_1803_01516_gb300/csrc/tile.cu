@@ -781,7 +781,7 @@ constexpr int kMaxPairs = 64;
 enum { PH_INIT = 0, PH_PASS = 1, PH_SWEEP = 2, PH_LABELS = 3, PH_DONE = 4 };
 
 struct PairState {
-    int phase, pass, full, conv, tail, status;
+    int phase, pass, full, conv, tail, status, cap;
     long long round, nrounds, rounds_total, relabels, passes, outer;
     long long active, prev1, prev2, relabel_visits, relabel_depth, last_relabel_depth, sweep_depth;
     long long visits_sweep_total, visits_relabel_total;
@@ -853,7 +853,7 @@ __device__ void advance(PairState &st, const SolveArgs &a, const long long v[4],
             if (v[1] == 0) {
                 st.conv = 1;
                 end = true;
-            } else if (!extract && !st.full && st.pass >= a.relabel_passes) {
+            } else if (!extract && !st.full && st.pass >= st.cap) {
                 end = true;
             } else {
                 st.pass++;
@@ -865,6 +865,9 @@ __device__ void advance(PairState &st, const SolveArgs &a, const long long v[4],
             }
             st.relabels++;
             st.last_relabel_depth = st.relabel_depth;
+            // a relabel run to its fixed point because the capped one reached no
+            // active node, and that found some: later relabels reach as far
+            if (st.full && st.active > 0) st.cap = max(st.cap, st.pass);
             st.visits_relabel_total += st.relabel_visits;
             if (st.active == 0) {
                 if (st.conv) {
@@ -956,6 +959,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
         PairState st;
         memset(&st, 0, sizeof(st));
         st.status = GS_OK;
+        st.cap = B.pair[p].relabel_passes;
         start_relabel(st, B.pair[p]);
         S[p] = st;
     }
@@ -1071,15 +1075,24 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
 // memory holds 9 int32 fields over the tile and a one-site halo; at most 8
 // nodes per thread (4 preferred).  Wider tiles first (coalesced rows of 32
 // sites), then the tallest that fits up to TH = 4.
-static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem) {
+static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int want_w = 0,
+                      int want_h = 0) {
     const size_t budget = 200 * 1024;
-    // squarish in sites first: a breadth-first path crosses fewer tile borders
-    static const int cand[][2] = {{16, 8}, {32, 4}, {16, 4}, {32, 2}, {16, 2}, {8, 4},
-                                  {16, 1}, {8, 2},  {8, 1},  {4, 2},  {4, 1}};
+    // more sites first, squarer first among equals: a breadth-first path then
+    // crosses fewer tile borders (measured: 8x8 beats 16x4 at 31 depth layers,
+    // 8x4 beats 16x2 at 47)
+    static const int cand[][2] = {{16, 8}, {8, 8}, {16, 4}, {32, 4}, {8, 4}, {32, 2},
+                                  {16, 2}, {4, 8}, {8, 2},  {4, 4},  {16, 1}, {8, 1},
+                                  {4, 2},  {4, 1}};
+    if (want_w || want_h) {
+        if (!(want_w == 4 || want_w == 8 || want_w == 16 || want_w == 32) || want_h < 1 ||
+            want_h > 8)
+            return false;
+    }
     for (int pass = 0; pass < 2; pass++) {
         const int max_nodes = (pass == 0 ? 4 : 8) * kTileThreads;
-        for (const auto &c : cand) {
-            const int TW = c[0], TH = c[1];
+        for (int ci = 0; ci < (want_w ? 1 : (int)(sizeof(cand) / sizeof(cand[0]))); ci++) {
+            const int TW = want_w ? want_w : cand[ci][0], TH = want_w ? want_h : cand[ci][1];
             const int TN = TH * g.K * TW;
             const int PN = (TH + 2) * g.K * (TW + 2);
             const size_t bytes = 9 * (size_t)PN * sizeof(int32_t);
@@ -1102,21 +1115,21 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem) {
     return false;
 }
 
+// Per-tile flags are sized for the most tiles any allowed shape gives (4 x 1
+// sites), so one workspace serves every tile shape.
+static int64_t max_tiles(const Geom &g) { return (int64_t)((g.ng + 3) / 4) * g.h; }
+
 size_t tiled_work_extra(const Geom &g) {
-    TileGeom t;
-    int npt;
-    size_t smem;
-    if (!pick_tile(g, t, npt, smem)) return 0;
-    return round_up(g.N * sizeof(uint16_t), 256) + round_up(5 * (int64_t)t.T * sizeof(int32_t), 256);
+    return round_up(g.N * sizeof(uint16_t), 256) + round_up(5 * max_tiles(g) * sizeof(int32_t), 256);
 }
 
 // Per-pair arguments from the pair's geometry, state and workspace.
-static int setup_args(const Geom &g, const State &s, const Work &w, SolveArgs &a, int &npt,
-                      size_t &smem) {
+static int setup_args(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
+                      SolveArgs &a, int &npt, size_t &smem) {
     memset(&a, 0, sizeof(a));
     a.g = g;
     a.s = s;
-    if (!pick_tile(g, a.t, npt, smem)) return GS_ERR_INVAL;
+    if (!pick_tile(g, a.t, npt, smem, o->tile_w, o->tile_h)) return GS_ERR_INVAL;
     char *extra = (char *)w.mark + round_up(g.N * sizeof(int32_t), 256);
     a.amask = (uint16_t *)extra;
     a.tile_act = (int32_t *)(extra + round_up(g.N * sizeof(uint16_t), 256));
@@ -1197,7 +1210,7 @@ int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opt
     B.extract = 0;
     int npt;
     size_t smem;
-    int rc = setup_args(g, s, w, B.pair[0], npt, smem);
+    int rc = setup_args(g, s, w, o, B.pair[0], npt, smem);
     if (rc) return rc;
     solve_fields(B.pair[0], o);
     B.pair[0].status = status;
@@ -1215,7 +1228,7 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
     B.extract = 1;
     int npt;
     size_t smem;
-    int rc = setup_args(g, s, w, B.pair[0], npt, smem);
+    int rc = setup_args(g, s, w, o, B.pair[0], npt, smem);
     if (rc) return rc;
     SolveArgs &a = B.pair[0];
     a.hgt = w.mark;
@@ -1230,13 +1243,13 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
 
 }  // namespace gs
 
-extern "C" int gs_tile_info(const gs_params *p, int32_t *out) {
+extern "C" int gs_tile_info(const gs_params *p, const gs_solve_opts *o, int32_t *out) {
     gs::Geom g;
-    if (gs::make_geom(p, &g) != GS_OK || !out) return GS_ERR_INVAL;
+    if (gs::make_geom(p, &g) != GS_OK || !o || !out) return GS_ERR_INVAL;
     gs::TileGeom t;
     int npt;
     size_t smem;
-    if (!gs::pick_tile(g, t, npt, smem)) return GS_ERR_INVAL;
+    if (!gs::pick_tile(g, t, npt, smem, o->tile_w, o->tile_h)) return GS_ERR_INVAL;
     out[0] = t.TW;
     out[1] = t.TH;
     out[2] = t.T;
@@ -1279,7 +1292,7 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
         const Work w = work_view(d.workspace, g);
         int npt;
         size_t smem;
-        if (setup_args(g, s, w, B.pair[i], npt, smem) != GS_OK) return GS_ERR_INVAL;
+        if (setup_args(g, s, w, &d.o, B.pair[i], npt, smem) != GS_OK) return GS_ERR_INVAL;
         solve_fields(B.pair[i], &d.o);
         B.pair[i].status = d.status;
         E.pair[i] = B.pair[i];

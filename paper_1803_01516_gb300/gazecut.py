@@ -46,6 +46,7 @@ class GsSolveOpts(ctypes.Structure):
                 ("fixed_sweeps", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("local_iters", ctypes.c_int32),
                 ("relabel_passes", ctypes.c_int32), ("tail_iters", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -90,11 +91,13 @@ class SolveOpts:
     local_iters: int = 0          # 0: library default
     relabel_passes: int = 0       # 0: library default
     tail_iters: int = 0           # 0: library default
+    tile_w: int = 0               # 0: library default
+    tile_h: int = 0
 
     def c(self) -> GsSolveOpts:
         return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, self.engine,
                            self.max_iters, self.local_iters, self.relabel_passes,
-                           self.tail_iters, 0)
+                           self.tail_iters, self.tile_w, self.tile_h, 0)
 
 
 _lib = None
@@ -126,7 +129,7 @@ def lib():
             "gs_solve_stats": ([P, P, P], ctypes.c_int),
             "gs_kernel_launches": ([], I64),
             "gs_noalloc_scratch_bytes": ([], SZ),
-            "gs_tile_info": ([pp, P], ctypes.c_int),
+            "gs_tile_info": ([pp, po, P], ctypes.c_int),
             "gs_stereo_cost_volume_f32": ([P, P, I32, pp, F, F, F, F, P, P], ctypes.c_int),
             "gs_energy_backward": ([P, pp, F, P, P, P], ctypes.c_int),
             "gs_cost_volume_f32_backward": ([P, P, I32, pp, F, F, F, P, P, P], ctypes.c_int),
@@ -283,9 +286,10 @@ def gs_kernel_launches() -> int:
     return int(lib().gs_kernel_launches())
 
 
-def gs_tile_info(p: Params) -> dict:
+def gs_tile_info(p: Params, o: SolveOpts | None = None) -> dict:
     out = (ctypes.c_int32 * 4)()
-    _check(lib().gs_tile_info(ctypes.byref(p.c()), out), "gs_tile_info")
+    o = o or SolveOpts()
+    _check(lib().gs_tile_info(ctypes.byref(p.c()), ctypes.byref(o.c()), out), "gs_tile_info")
     return {"tile_w": out[0], "tile_h": out[1], "tiles": out[2], "smem_bytes": out[3]}
 
 
