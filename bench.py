@@ -477,9 +477,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gazecut", choices=["gazecut", "reference"])
-    ap.add_argument("--sweeps-per-relabel", type=int, default=8)
+    ap.add_argument("--sweeps-per-relabel", type=int, default=16)
     ap.add_argument("--local-iters", type=int, default=8)
-    ap.add_argument("--relabel-passes", type=int, default=4)
+    ap.add_argument("--relabel-passes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=64)

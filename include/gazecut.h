@@ -94,7 +94,7 @@ typedef struct gs_solve_opts {
     int64_t max_iters;           /* cap on global relabels in exact mode (> 0) */
     int32_t local_iters;         /* TILED: push/relabel iterations per tile visit (0: 8) */
     int32_t relabel_passes;      /* TILED: tile passes of an intermediate global relabel
-                                    (0: 4); the relabel that decides termination always
+                                    (0: 8); the relabel that decides termination always
                                     runs to its fixed point */
     int32_t tail_iters;          /* TILED: local iterations per tile visit once few nodes
                                     are active (0: 4 x local_iters) */

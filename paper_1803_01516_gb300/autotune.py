@@ -23,7 +23,7 @@ import torch
 from . import gazecut as gc
 from . import synth
 
-SCHEDULES = [(spr, li, rp) for spr in (4, 8, 16, 32) for li in (4, 8, 16) for rp in (4, 8, 16)]
+SCHEDULES = [(spr, li, rp) for spr in (8, 16, 32) for li in (8, 16) for rp in (4, 8, 16)]
 SHAPES = [(16, 8), (8, 8), (16, 4), (32, 4), (8, 4), (16, 2), (8, 2), (4, 4)]
 
 
@@ -33,9 +33,29 @@ def cache_path() -> str:
                                        "autotune.json"))
 
 
+def _key(D: int, nodes: int):
+    return 8 * int(round(D / 8)), int(round(math.log2(max(nodes, 1))))
+
+
 def bucket(p: gc.Params) -> str:
-    nodes = max(p.ng * p.h * (p.D - 1), 1)
-    return f"D{p.D}-n{int(round(math.log2(nodes)))}"
+    """(depth numbers rounded to a multiple of 8, log2 of the node count)."""
+    d, n = _key(p.D, p.ng * p.h * (p.D - 1))
+    return f"D{d}-n{n}"
+
+
+def _nearest(table: dict, p: gc.Params):
+    """Entry of the bucket nearest to p's (same depth group first)."""
+    d, n = _key(p.D, p.ng * p.h * (p.D - 1))
+    best, dist = None, None
+    for k, v in table.items():
+        try:
+            kd, kn = (int(x[1:]) for x in k.split("-"))
+        except ValueError:
+            continue
+        dd = abs(kd - d) * 4 + abs(kn - n)
+        if dist is None or dd < dist:
+            best, dist = v, dd
+    return best
 
 
 def _load() -> dict:
@@ -71,7 +91,10 @@ def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
             gc.gs_build_graph(buf.cost, p, buf.graph, buf.status)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+            try:
+                gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+            except RuntimeError:
+                return float("inf")
             b.record()
             b.synchronize()
             if int(buf.status.item()) != gc.GS_OK:
@@ -81,7 +104,7 @@ def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
     return ts[len(ts) // 2]
 
 
-def tune(p: gc.Params, n_pairs: int = 2, save: bool = True) -> dict:
+def tune(p: gc.Params, n_pairs: int = 1, save: bool = True) -> dict:
     """Tile shape first (default schedule), then the schedule on the best shape,
     each measured on synthetic pairs of p's size."""
     wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
@@ -122,6 +145,8 @@ def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpt
     entry = _load().get(bucket(p)) or _defaults().get(bucket(p))
     if entry is None and tune_if_missing:
         entry = tune(p)
+    if entry is None:
+        entry = _nearest(_load(), p) or _nearest(_defaults(), p)
     if entry is None:
         return gc.SolveOpts(**kw)
     best = entry["best"]

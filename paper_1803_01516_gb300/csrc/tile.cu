@@ -1077,7 +1077,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
 // sites), then the tallest that fits up to TH = 4.
 static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int want_w = 0,
                       int want_h = 0) {
-    const size_t budget = 200 * 1024;
+    // dynamic shared memory of a tile; with the kernel's ~42 KB of static
+    // shared arrays it must stay under the 227 KB a block may opt in to
+    const size_t budget = 180 * 1024;
     // more sites first, squarer first among equals: a breadth-first path then
     // crosses fewer tile borders (measured: 8x8 beats 16x4 at 31 depth layers,
     // 8x4 beats 16x2 at 47)
@@ -1145,7 +1147,7 @@ static void solve_fields(SolveArgs &a, const gs_solve_opts *o) {
     a.mode = o->mode;
     a.sweeps_per_relabel = o->sweeps_per_relabel;
     a.local_iters = o->local_iters > 0 ? o->local_iters : 8;
-    a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 4;
+    a.relabel_passes = o->relabel_passes > 0 ? o->relabel_passes : 8;
     a.tail_iters = o->tail_iters > 0 ? o->tail_iters : 4 * a.local_iters;
     a.fixed_sweeps = o->fixed_sweeps;
     a.max_iters = o->max_iters;

@@ -84,7 +84,7 @@ class SolveOpts:
     """Solver options (mirrors ``gs_solve_opts``)."""
 
     mode: int = GS_MODE_EXACT
-    sweeps_per_relabel: int = 8
+    sweeps_per_relabel: int = 16
     fixed_sweeps: int = 0
     max_iters: int = 1 << 16
     engine: int = GS_ENGINE_TILED
