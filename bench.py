@@ -65,7 +65,7 @@ def _profiled_traffic():
     """DRAM bytes per launch of the solve kernel from the committed ncu summary,
     or None when the kernel source changed since that capture."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_solve_tiled_main-384x288x16.md")
+    prof = os.path.join(ROOT, "profiles", "k_batch_main-384x288x16.md")
     src = os.path.join(ROOT, "paper_1803_01516_gb300", "csrc", "tile.cu")
     try:
         kv = {}
@@ -444,7 +444,7 @@ def run(args):
                                "local_iters": o.local_iters, "relabel_passes": o.relabel_passes,
                                "replicas": world, "tile": [ti["tile_w"], ti["tile_h"]]}),
         "e2e": e2e,
-        "roofline": {"bound": "hbm", "kernel": "k_solve_tiled", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_batch (max-flow)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _profiled_traffic(),
                      "peak_kind": f"{peak_kind} HBM copy",
