@@ -164,6 +164,23 @@ def _cpu_baseline(wl, pairs):
     return cpu, refs
 
 
+def _reduce_max(ms: float, dist, device) -> float:
+    """The job's time is the slowest replica's: max over ranks (no other
+    collective: each rank solves its own pairs)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_pairs(rank: int, n: int = None):
+    """Seeded pair indices of a replica: disjoint across ranks."""
+    n = N_PAIRS if n is None else n
+    return [rank * n + i for i in range(n)]
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -307,7 +324,7 @@ def run(args):
     o = gc.SolveOpts(sweeps_per_relabel=args.sweeps_per_relabel, local_iters=args.local_iters,
                      relabel_passes=args.relabel_passes)
     # each rank solves its own pairs (replicas)
-    pairs = [synth.make_pair(wl, rank * N_PAIRS + i) for i in range(N_PAIRS)]
+    pairs = [synth.make_pair(wl, i) for i in replica_pairs(rank)]
     Ld = [torch.from_numpy(L).to(dev) for L, _, _ in pairs]
     Rd = [torch.from_numpy(R).to(dev) for _, R, _ in pairs]
     buf = gc.Buffers(p, o, device=dev)
@@ -368,12 +385,7 @@ def run(args):
     clk = clocks.stop() if rank == 0 else None
     if bad_status:
         raise RuntimeError("a timed solve did not end with GS_OK")
-    if dist:
-        t = torch.tensor([my_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    else:
-        tot_ms = my_ms
+    tot_ms = _reduce_max(my_ms, dist, dev)
     total_pairs = args.steps * world
     value = tot_ms / total_pairs
 
