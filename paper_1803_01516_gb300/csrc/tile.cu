@@ -357,51 +357,34 @@ template <int NPT>
 __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi)[NPT],
                            const unsigned (&mk)[NPT]) {
     const TileGeom &t = a.t;
-    const int K = a.g.K;
-    const int R = t.TH * K;
-    const int RW = (R + 31) >> 5;
-    __shared__ unsigned dirty[3][kMaxRows / 32];
     int off[kSlots];
 #pragma unroll
     for (int q = 0; q < kSlots; q++) off[q] = soff(t, q);
-    for (int w = threadIdx.x; w < 3 * (kMaxRows / 32); w += blockDim.x) (&dirty[0][0])[w] = 0;
-    __syncthreads();
-    int row[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; k++) row[k] = (threadIdx.x + k * blockDim.x) / t.TW;
+    // Asynchronous (chaotic) relaxation: each thread sweeps its nodes
+    // kInner times between CTA barriers, reading neighbours' heights as other
+    // warps update them.  Values only decrease and stay upper bounds, so any
+    // interleaving converges to the same fixed point; an outer round in which
+    // no height changed anywhere proves it has been reached.
+    constexpr int kInner = 4;
+    volatile int32_t *ht = m.ht;
     bool any_change = false;
-    for (int iter = 0;; iter++) {
-        const unsigned *cur = dirty[iter % 3];
-        unsigned *nxt = dirty[(iter + 1) % 3];
-        unsigned *clr = dirty[(iter + 2) % 3];
-        for (int w = threadIdx.x; w < RW; w += blockDim.x) clr[w] = 0;
+    for (int outer = 0;; outer++) {
         int changed = 0;
+        for (int inner = 0; inner < kInner; inner++) {
 #pragma unroll
-        for (int k = 0; k < NPT; k++) {
-            if (pi[k] < 0) continue;
-            const int r = row[k];
-            if (iter > 0) {
-                bool dep = false;
+            for (int k = 0; k < NPT; k++) {
+                if (pi[k] < 0) continue;
+                const int32_t h = ht[pi[k]];
+                if (h == 0) continue;
+                int32_t hmin = kInfH;
+                const unsigned bits = mk[k] & 0x3fffu;
 #pragma unroll
-                for (int dy = -1; dy <= 1; dy++)
-#pragma unroll
-                    for (int dj = -1; dj <= 1; dj++) {
-                        const int rr = r + dy * K + dj;
-                        if (rr >= 0 && rr < R) dep |= (cur[rr >> 5] >> (rr & 31)) & 1u;
-                    }
-                if (!dep) continue;
-            }
-            const int32_t h = m.ht[pi[k]];
-            if (h == 0) continue;
-            int32_t hmin = kInfH;
-            const unsigned bits = mk[k] & 0x3fffu;
-#pragma unroll
-            for (int q = 0; q < kSlots; q++)
-                if (bits & (1u << q)) hmin = min(hmin, m.ht[pi[k] + off[q]]);
-            if (hmin < kInfH && hmin + 1 < h) {
-                m.ht[pi[k]] = hmin + 1;
-                atomicOr(&nxt[r >> 5], 1u << (r & 31));
-                changed = 1;
+                for (int q = 0; q < kSlots; q++)
+                    if (bits & (1u << q)) hmin = min(hmin, ht[pi[k] + off[q]]);
+                if (hmin < kInfH && hmin + 1 < h) {
+                    ht[pi[k]] = hmin + 1;
+                    changed = 1;
+                }
             }
         }
         if (!__syncthreads_or(changed)) break;
@@ -785,6 +768,7 @@ struct PairState {
     long long round, nrounds, rounds_total, relabels, passes, outer;
     long long active, prev1, prev2, relabel_visits, relabel_depth, last_relabel_depth, sweep_depth;
     long long visits_sweep_total, visits_relabel_total;
+    long long ns_sweep, ns_relabel;    // device time of the steps in each phase (block 0's clock)
 };
 
 struct BatchArgs {
@@ -964,6 +948,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
         S[p] = st;
     }
     __syncthreads();
+    unsigned long long t_step = now_ns();
     for (long long step = 0;; step++) {
         long long *red = B.red + (step % 3) * B.n * 4;
         for (int gt = blockIdx.x; gt < B.T_total; gt += gridDim.x) {
@@ -1032,12 +1017,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
         grid_sync_sum(B.bar, 0);
         if (aborted(B.bar)) break;
         int done = 1;
+        const unsigned long long t_now = now_ns();
         for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
             long long v[4];
             for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&red[p * 4 + k];
+            if (S[p].phase == PH_SWEEP) S[p].ns_sweep += (long long)(t_now - t_step);
+            else if (S[p].phase != PH_DONE) S[p].ns_relabel += (long long)(t_now - t_step);
             advance(S[p], B.pair[p], v, B.extract);
             done &= S[p].phase == PH_DONE;
         }
+        t_step = t_now;
         if (__syncthreads_and(done)) break;
     }
     // per-pair results (block 0): statistics, flow value, status
@@ -1054,8 +1043,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                 c->stats[1] = st.rounds_total;
                 c->stats[2] = st.passes;
                 c->stats[4] = st.active;
-                c->stats[5] = 0;
-                c->stats[6] = 0;
+                c->stats[5] = st.ns_sweep;
+                c->stats[6] = st.ns_relabel;
                 c->stats[7] = 1;
                 c->visits_sweep = st.visits_sweep_total;
                 c->visits_relabel = st.visits_relabel_total;
