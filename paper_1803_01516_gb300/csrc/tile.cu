@@ -625,51 +625,55 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
         slot_delta(q, dy, dj, dw);
         goff[q] = dy * g.SY + (int64_t)dj * g.P + dw;
     }
-    // Each local iteration first compacts the tile's active nodes (positive
-    // excess, finite height) into a list, then discharges the list densely, so
-    // warps do not idle on inactive lanes.
-    __shared__ int s_nact[2];
-    __shared__ uint16_t s_list[kMaxTileNodes];
+    // Local iterations, one warp at a time and with no block barrier: each
+    // warp compacts its own active nodes (positive excess, finite height; the
+    // nodes its lanes own) into a warp list with ballots, discharges the list
+    // 32 nodes at a time, and goes on to its next iteration.  Discharges of
+    // different warps run concurrently on shared memory; the lock-free argument
+    // that holds between tiles holds between warps (only a node's own warp
+    // lowers its excess, and residuals are consumed only by an arc's tail).
+    __shared__ uint16_t s_wlist[kTileThreads / 32][4 * 32 * 2];
     const int64_t tile_g0 = (int64_t)o.y0 * g.SY + o.W0;
-    if (threadIdx.x == 0) s_nact[0] = s_nact[1] = 0;
-    __syncthreads();
     unsigned nb_touch = 0;   // bit 0: left, 1: right, 2: up, 3: down neighbour tile received flow
     const int lane = threadIdx.x & 31;
+    uint16_t *wl_list = s_wlist[threadIdx.x >> 5];
+    volatile int32_t *vex = m.ex;
+    volatile int32_t *vht = m.ht;
     for (int it = 0; it < iters; it++) {
-        int *cnt = &s_nact[it & 1];
+        int cnt = 0;
 #pragma unroll
         for (int k = 0; k < NPT; k++) {
-            const bool act = pi[k] >= 0 && m.ex[pi[k]] > 0 && m.ht[pi[k]] < kInfH;
+            const bool act = pi[k] >= 0 && vex[pi[k]] > 0 && vht[pi[k]] < kInfH;
             const unsigned bal = __ballot_sync(0xffffffffu, act);
-            if (bal) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(cnt, __popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (act) s_list[base + __popc(bal & ((1u << lane) - 1u))] =
-                    (uint16_t)(threadIdx.x + k * blockDim.x);
-            }
+            if (act) wl_list[cnt + __popc(bal & ((1u << lane) - 1u))] =
+                (uint16_t)(threadIdx.x + k * blockDim.x);
+            cnt += __popc(bal);
         }
-        __syncthreads();
-        const int nact = *cnt;
-        if (threadIdx.x == 0) s_nact[(it + 1) & 1] = 0;
-        if (nact == 0) break;
-        for (int li = threadIdx.x; li < nact; li += blockDim.x) {
-            const int n = s_list[li];
+        __syncwarp();
+        if (cnt == 0) continue;
+        for (int li = lane; li < cnt; li += 32) {
+            const int n = wl_list[li];
             const uint32_t info = s_info[n];
             const int p = (int)(info & 0xffffu);
             const int wl = (int)((info >> 16) & 31u), yl = (int)((info >> 21) & 15u);
             const int j = (int)(info >> 25);
             const int64_t gin = tile_g0 + (int64_t)yl * g.SY + (int64_t)j * g.P + wl;
             const unsigned exb = s_exb[n];
-            const int32_t e = m.ex[p];
-            const int32_t hu = m.ht[p];
+            const int32_t e = vex[p];
+            const int32_t hu = vht[p];
             if (e <= 0 || hu >= kInfH) continue;
             int32_t rr[kSlots], hv[kSlots];
+            // all loads issued before any is used (the existing arcs' heights
+            // are read whatever their residual), so they overlap
 #pragma unroll
             for (int q = 0; q < kSlots; q++) {
-                rr[q] = ((exb >> q) & 1u) ? smem_residual(m, t, g, p, q) : 0;
-                hv[q] = rr[q] > 0 ? m.ht[p + off[q]] : kInfH;
+                const bool ex = (exb >> q) & 1u;
+                rr[q] = ex ? smem_residual(m, t, g, p, q) : 0;
+                hv[q] = vht[p + (ex ? off[q] : 0)];
             }
+#pragma unroll
+            for (int q = 0; q < kSlots; q++)
+                if (rr[q] <= 0) hv[q] = kInfH;
             int32_t left = e;
 #pragma unroll
             for (int q = 0; q < kSlots; q++) {
@@ -699,10 +703,10 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
 #pragma unroll
                 for (int q = 0; q < kSlots; q++)
                     if (rr[q] > 0) hmin = min(hmin, hv[q]);
-                m.ht[p] = hmin >= kInfH - 1 ? kInfH : hmin + 1;
+                vht[p] = hmin >= kInfH - 1 ? kInfH : hmin + 1;
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
     __syncthreads();
     // write back own nodes as deltas (other tiles may have updated the same
