@@ -71,6 +71,9 @@ typedef struct gs_params {
     int32_t lambda;            /* penalty h~1 (smoothness), 0 <= lambda <= 2^28 */
     int32_t inhibit;           /* inhibit h~2 (visibility), 0 <= inhibit <= 2^29 */
     int32_t vertical_inhibit;  /* 1: inhibit on vertical pairs too; 0: horizontal pairs only */
+    int32_t direction;         /* max-flow direction: 0 auto, 1 as given, 2 label-reversed
+                                  (the reversed graph; same min energy and canonical labels).
+                                  Auto takes the side with the smaller source capacity. */
 } gs_params;
 
 /* Solve modes. */

@@ -15,6 +15,7 @@ int make_geom(const gs_params *p, Geom *g) {
     if (p->lambda < 0 || p->lambda > (1 << 28)) return GS_ERR_INVAL;
     if (p->inhibit < 0 || p->inhibit > (1 << 29)) return GS_ERR_INVAL;
     if (p->tau < 0) return GS_ERR_INVAL;
+    if (p->direction < 0 || p->direction > 2) return GS_ERR_INVAL;
     g->ng = p->w - p->dis0;
     g->h = p->h;
     g->D = p->D;

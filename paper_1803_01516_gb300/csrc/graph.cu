@@ -28,10 +28,28 @@ __global__ void k_header(GraphHeader *hdr, Geom g, int inhibit, int vinhibit) {
     hdr->lam = g.lam;
     hdr->inhibit = inhibit;
     hdr->vinhibit = vinhibit;
-    hdr->base_flow = 0;
+    hdr->rev = 0;
+    hdr->sum_first = 0;
     hdr->init_deficit = 0;
     hdr->src_total = 0;
-    hdr->max_cost = 0;
+    hdr->sum_last = 0;
+}
+
+// Source capacity of each direction: sum of C(0) and of C(D-1).
+__global__ void k_dir_sums(const int32_t *__restrict__ C, Geom g, GraphHeader *hdr) {
+    unsigned long long a = 0, b = 0;
+    const int64_t sites = (int64_t)g.ng * g.h;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < sites;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        a += (unsigned long long)max(C[v * g.D], 0);
+        b += (unsigned long long)max(C[v * g.D + g.D - 1], 0);
+    }
+    block_sum_u64(a, &hdr->sum_first);
+    block_sum_u64(b, &hdr->sum_last);
+}
+
+__global__ void k_decide(GraphHeader *hdr, int direction) {
+    hdr->rev = direction == 2 ? 1 : direction == 1 ? 0 : (hdr->sum_last < hdr->sum_first ? 1 : 0);
 }
 
 // One thread per node.  Chain node j = k-1 of site (W, y); its incoming data
@@ -48,6 +66,7 @@ __global__ void k_header(GraphHeader *hdr, Geom g, int inhibit, int vinhibit) {
 __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t *status) {
     unsigned long long deficit = 0, src = 0;
     int bad = 0, big = 0;
+    const bool rev = *(volatile int32_t *)&s.hdr->rev != 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const NodePos p = node_pos(g, i);
@@ -58,12 +77,14 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
             s.ht[i] = kInfH;
             continue;
         }
-        const int32_t *c = C + ((int64_t)p.y * g.ng + p.W) * g.D;
-        int32_t F = c[0];                 // F_j
+        const int32_t *cs = C + ((int64_t)p.y * g.ng + p.W) * g.D;
+        // cost of label l in the direction solved
+        auto c = [&](int l) { return cs[rev ? g.D - 1 - l : l]; };
+        int32_t F = c(0);                 // F_j
         bad |= F < 0;
         big |= F > kCapLimit;
-        for (int q = 1; q <= p.j; q++) F = min(F, c[q]);
-        const int32_t cout = c[p.j + 1];  // outgoing arc capacity
+        for (int q = 1; q <= p.j; q++) F = min(F, c(q));
+        const int32_t cout = c(p.j + 1);  // outgoing arc capacity
         bad |= cout < 0;
         big |= cout > kCapLimit;
         int32_t e, rc;
@@ -76,7 +97,7 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
             rc = 0;
             deficit += (unsigned long long)max(cout, 0);
         }
-        if (p.j == 0) src += (unsigned long long)max(c[0], 0);
+        if (p.j == 0) src += (unsigned long long)max(c(0), 0);
         s.rc[i] = rc;
         s.ex[i] = e;
         s.rr[i] = (p.W < g.ng - 1) ? g.lam : 0;
@@ -163,6 +184,12 @@ __global__ void k_labels(Geom g, State s, const int32_t *mark, int use_heights, 
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_LABELS);
 }
 
+__global__ void k_flip_labels(int32_t *labels, int64_t n, int D) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        labels[v] = D - 1 - labels[v];
+}
+
 __global__ void k_deficit(Geom g, State s, unsigned long long *out) {
     unsigned long long d = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
@@ -174,7 +201,7 @@ __global__ void k_deficit(Geom g, State s, unsigned long long *out) {
 }
 
 __global__ void k_flow(const GraphHeader *hdr, const Ctrl *ctrl, int64_t *flow) {
-    *flow = (int64_t)hdr->base_flow + (int64_t)hdr->init_deficit - (int64_t)ctrl->deficit_left;
+    *flow = (int64_t)hdr->init_deficit - (int64_t)ctrl->deficit_left;
 }
 
 }  // namespace gs
@@ -202,9 +229,11 @@ int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t
     State s = state_view(graph, g);
     GS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
     k_header<<<1, 1, 0, st>>>(s.hdr, g, p->inhibit, p->vertical_inhibit);
+    k_dir_sums<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(cost, g, s.hdr);
+    k_decide<<<1, 1, 0, st>>>(s.hdr, p->direction);
     k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
     k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
-    count_launches(3);
+    count_launches(5);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -219,7 +248,10 @@ int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, v
     Work w = work_view(workspace, g);
     if (o->engine == GS_ENGINE_TILED) return tiled_extract(g, s, w, o, labels, flow, status, st);
     const int grid = grid_for(g.N);
-    if (o->mode == GS_MODE_EXACT) {
+    int32_t rev = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&rev, &s.hdr->rev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (o->mode == GS_MODE_EXACT && !rev) {
         k_mark_init<<<grid, 256, 0, st>>>(g, s, w.mark);
         count_launches(1);
         int64_t passes = 0;
@@ -244,8 +276,16 @@ int gs_extract_labels(void *graph, const gs_params *p, const gs_solve_opts *o, v
         int64_t passes = 0;
         int rc = global_relabel(g, s, w, st, &passes);
         if (rc) return rc;
+        // the largest minimiser of the solved direction (nodes that cannot
+        // reach sink capacity); for a label-reversed state it maps back to the
+        // smallest minimiser of the original problem
         k_labels<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(g, s, w.mark, 1, labels, status);
         count_launches(1);
+        if (rev) {
+            k_flip_labels<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(labels, (int64_t)g.ng * g.h,
+                                                                      g.D);
+            count_launches(1);
+        }
     }
     GS_CUDA_TRY(cudaMemsetAsync(&w.ctrl->deficit_left, 0, sizeof(unsigned long long), st));
     k_deficit<<<grid, 256, 0, st>>>(g, s, &w.ctrl->deficit_left);

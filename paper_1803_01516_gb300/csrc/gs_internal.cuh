@@ -33,14 +33,20 @@ struct Geom {
 };
 
 // Header at the start of the graph buffer (256 bytes reserved).
+// The graph may be built for the label-reversed problem C'(l) = C(D-1-l): it
+// is the reversed graph (sources and sinks swapped, arcs reversed), has the
+// same minimum energy, and its largest minimiser X'max gives the canonical
+// smallest minimiser of the original as X = D-1-X'max.  build_graph picks the
+// direction with the smaller total source capacity (less excess to route)
+// unless the caller fixes it.
 struct GraphHeader {
     uint32_t magic;
-    int32_t D, ng, h, K, P, lam, inhibit, vinhibit, pad0;
-    unsigned long long base_flow;     // flow routed s -> n -> t inside one node (D == 2)
+    int32_t D, ng, h, K, P, lam, inhibit, vinhibit;
+    int32_t rev;                      // 1: the state is the label-reversed problem
+    unsigned long long sum_first;     // sum of C(0) over sites
     unsigned long long init_deficit;  // total sink capacity left after folding
     unsigned long long src_total;     // total source capacity
-    int32_t max_cost;
-    int32_t pad1;
+    unsigned long long sum_last;      // sum of C(D-1) over sites
 };
 
 // Solver state: structure of arrays, each N int32, 256-byte aligned.

@@ -55,7 +55,9 @@ struct SolveArgs {
     int32_t *tile_cnt;   // [T] active nodes per tile after its last relabel pass
     int32_t *hgt;        // distances the relabel passes compute (state heights, or marks)
     int dir;             // 0: distance to sink capacity over out-arcs (heights);
-                         // 1: distance from positive excess over in-arcs (reachability)
+                         // 1: distance from positive excess over in-arcs (reachability);
+                         // 2: label extraction of an exact solve, 1 unless the state is
+                         //    the label-reversed problem, then 0
     Ctrl *ctrl;          // the pair's control block (statistics)
     int32_t *status;     // the caller's device status word
     int32_t *labels;     // label extraction output [h][n_g]
@@ -344,6 +346,12 @@ __device__ void load_halo(const SolveArgs &a, const TileSmem &m, const TileOrigi
     }
 }
 
+// Search direction of a relabel pass (see SolveArgs::dir).
+__device__ __forceinline__ int eff_dir(const SolveArgs &a) {
+    if (a.dir != 2) return a.dir;
+    return ld(&a.s.hdr->rev) ? 0 : 1;
+}
+
 // ---------------------------------------------------------- relabel pass ---
 
 // Local relaxation to the tile's fixed point.  Own nodes' residual-arc masks
@@ -403,6 +411,7 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
     const TileGeom &t = a.t;
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
+    const int dir = eff_dir(a);
     load_halo(a, m, o, true, a.hgt);
     int pi[NPT];
     unsigned mk[NPT];
@@ -432,7 +441,7 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
         m.ri2[p] = ld(&s.ri2[i]);
         m.ri3[p] = ld(&s.ri3[i]);
         const int32_t e = ld(&s.ex[i]);
-        if (a.dir == 0) {
+        if (dir == 0) {
             m.ht[p] = e < 0 ? 0 : kInfH;
             mk[k] = e > 0 ? 0x8000u : 0u;
         } else {
@@ -450,7 +459,7 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
         for (int q = 0; q < kSlots; q++) {
             if (!((ex >> q) & 1u)) continue;
             bool res;
-            if (a.dir == 0) {
+            if (dir == 0) {
                 res = smem_residual(m, t, g, pi[k], q) > 0;          // arc u -> head
             } else if (q == 0) {
                 res = true;                                           // head j+1 -> u: infinite
@@ -917,6 +926,8 @@ __device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
     const TileOrigin o = tile_origin(t, tile);
     unsigned long long deficit = 0;
     int b = 0;
+    const int dir = eff_dir(a);
+    const bool rev = ld(&a.s.hdr->rev) != 0;
     for (int sidx = threadIdx.x; sidx < t.TW * t.TH; sidx += blockDim.x) {
         const int wl = sidx % t.TW, yl = sidx / t.TW;
         const int W = o.W0 + wl, y = o.y0 + yl;
@@ -925,14 +936,14 @@ __device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
         int lab = 0, prev = 1;
         for (int j = 0; j < g.K; j++, i += g.P) {
             const int32_t h = ld(&a.hgt[i]);
-            const int in = a.dir == 1 ? (h < kInfH) : (h >= kInfH);
+            const int in = dir == 1 ? (h < kInfH) : (h >= kInfH);
             b |= in && !prev;
             lab += in;
             prev = in;
             const int32_t e = ld(&a.s.ex[i]);
             if (e < 0) deficit += (unsigned long long)(-(int64_t)e);
         }
-        a.labels[(int64_t)y * g.ng + W] = lab;
+        a.labels[(int64_t)y * g.ng + W] = rev ? g.D - 1 - lab : lab;
     }
     bad = __syncthreads_or(b);
     return block_sum((long long)deficit);
@@ -1227,7 +1238,7 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
     if (rc) return rc;
     SolveArgs &a = B.pair[0];
     a.hgt = w.mark;
-    a.dir = o->mode == GS_MODE_EXACT ? 1 : 0;
+    a.dir = o->mode == GS_MODE_EXACT ? 2 : 0;
     a.mode = GS_MODE_EXACT;
     a.max_iters = 1;
     a.labels = labels;
@@ -1293,7 +1304,7 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
         E.pair[i] = B.pair[i];
         SolveArgs &x = E.pair[i];
         x.hgt = w.mark;
-        x.dir = d.o.mode == GS_MODE_EXACT ? 1 : 0;
+        x.dir = d.o.mode == GS_MODE_EXACT ? 2 : 0;
         x.mode = GS_MODE_EXACT;
         x.max_iters = 1;
         x.labels = d.labels;

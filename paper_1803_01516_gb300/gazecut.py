@@ -38,7 +38,8 @@ EXPORTS = [
 class GsParams(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("D", ctypes.c_int32),
                 ("dis0", ctypes.c_int32), ("tau", ctypes.c_int32), ("lambda_", ctypes.c_int32),
-                ("inhibit", ctypes.c_int32), ("vertical_inhibit", ctypes.c_int32)]
+                ("inhibit", ctypes.c_int32), ("vertical_inhibit", ctypes.c_int32),
+                ("direction", ctypes.c_int32)]
 
 
 class GsSolveOpts(ctypes.Structure):
@@ -68,11 +69,12 @@ class Params:
     inhibit: int = 1023
     vertical_inhibit: int = 1
     dis0: int | None = None      # default 2(D-1): depth covers disparities 0..2(D-1)
+    direction: int = 0           # 0 auto, 1 as given, 2 label-reversed
 
     def c(self) -> GsParams:
         dis0 = 2 * (self.D - 1) if self.dis0 is None else self.dis0
         return GsParams(self.w, self.h, self.D, dis0, self.tau, self.lam, self.inhibit,
-                        self.vertical_inhibit)
+                        self.vertical_inhibit, self.direction)
 
     @property
     def ng(self) -> int:

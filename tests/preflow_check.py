@@ -6,7 +6,8 @@ labeling X.  So a state that is a valid preflow, plus labels whose energy
 (computed independently by the oracle) equals F, proves both optimal -- at
 sizes the oracle cannot solve.
 
-The state layout is the library's: a 256-byte header, then nine int32 arrays
+The state layout is the library's: a 256-byte header (int32 at byte 36 = 1
+when the state is the label-reversed problem), then nine int32 arrays
 (rc, rr, rd, ri0, ri1, ri2, ri3, ex, ht), each over the padded node grid
 [h][K][P] (K = D-1, P = n_g rounded up to 32) and padded to 64 entries.
 Flows are read back from residuals: data arc n_j -> n_(j+1) carries
@@ -37,6 +38,10 @@ def check_preflow(graph_bytes: np.ndarray, C: np.ndarray, lam: int, inhibit: int
     h, ng, D = C.shape
     K = D - 1
     s = state_arrays(graph_bytes, h, ng, D)
+    # a state built for the label-reversed problem uses C'(l) = C(D-1-l)
+    rev = int(graph_bytes[36:40].view(np.int32)[0])
+    if rev:
+        C = C[:, :, ::-1]
     Ct = np.transpose(C, (0, 2, 1)).astype(np.int64)          # [h][D][ng]
     h2h, h2v = inhibit, (inhibit if vinhibit else 0)
     rc, rr, rd, ex = s["rc"], s["rr"], s["rd"], s["ex"]

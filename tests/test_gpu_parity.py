@@ -24,9 +24,10 @@ def _params(gc, wl, vi=1):
                      vertical_inhibit=vi)
 
 
-def _solve_costs(gc, C, lam, inhibit, vi, opts=None):
+def _solve_costs(gc, C, lam, inhibit, vi, opts=None, direction=0):
     h, ng, D = C.shape
-    p = gc.Params(w=ng + 2 * (D - 1), h=h, D=D, tau=0, lam=lam, inhibit=inhibit, vertical_inhibit=vi)
+    p = gc.Params(w=ng + 2 * (D - 1), h=h, D=D, tau=0, lam=lam, inhibit=inhibit, vertical_inhibit=vi,
+                  direction=direction)
     opts = opts or gc.SolveOpts()
     labels, flow, status = gc.solve_costs(torch.from_numpy(np.ascontiguousarray(C)).cuda(), p, opts)
     torch.cuda.synchronize()
@@ -78,24 +79,27 @@ def test_tiny_pair_exact(gc, vi, engine):
     ((11, 97, 16), 10, 1023, 1, 30),  # several tiles in both directions
 ])
 @pytest.mark.parametrize("engine", ENGINES)
-def test_random_costs_exact(gc, shape, lam, inh, vi, hi, engine):
+@pytest.mark.parametrize("direction", [1, 2])
+def test_random_costs_exact(gc, shape, lam, inh, vi, hi, engine, direction):
+    """Both solve directions (as given, label-reversed) give the canonical cut."""
     rng = np.random.default_rng(sum(shape) * 7 + lam)
     C = rng.integers(0, hi + 1, size=shape).astype(np.int32)
-    X, flow, status, _ = _solve_costs(gc, C, lam, inh, vi, gc.SolveOpts(engine=engine))
+    X, flow, status, _ = _solve_costs(gc, C, lam, inh, vi, gc.SolveOpts(engine=engine), direction)
     ref = oracle.solve(C, lam, inh, vi)
     assert status == gc.GS_OK
     assert flow == ref["flow"]
     assert np.array_equal(X, ref["labels"])
 
 
-def test_ties_canonical_labels(gc):
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_ties_canonical_labels(gc, direction):
     """Constant costs: every constant labeling is optimal; the canonical answer
-    is the smallest one (all zeros)."""
+    is the smallest one (all zeros), in either solve direction."""
     C = np.full((10, 40, 6), 7, dtype=np.int32)
-    X, flow, status, _ = _solve_costs(gc, C, 3, 1023, 1)
+    X, flow, status, _ = _solve_costs(gc, C, 3, 1023, 1, direction=direction)
     assert status == gc.GS_OK and flow == 7 * 400 and (X == 0).all()
     C = np.random.default_rng(0).integers(0, 3, size=(12, 35, 4)).astype(np.int32)
-    X, flow, status, _ = _solve_costs(gc, C, 1, 2, 1)
+    X, flow, status, _ = _solve_costs(gc, C, 1, 2, 1, direction=direction)
     ref = oracle.solve(C, 1, 2, 1)
     assert flow == ref["flow"] and np.array_equal(X, ref["labels"])
     assert (ref["labels"] != ref["labels_max"]).any()
@@ -129,7 +133,8 @@ def test_energy_kernel_matches_oracle(gc):
 
 
 @pytest.mark.parametrize("engine", ENGINES)
-def test_fixed_sweeps_gap_is_nonnegative(gc, engine):
+@pytest.mark.parametrize("direction", [1, 2])
+def test_fixed_sweeps_gap_is_nonnegative(gc, engine, direction):
     wl = synth.TINY
     L, R, _ = synth.make_pair(wl, 1)
     C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
@@ -137,7 +142,7 @@ def test_fixed_sweeps_gap_is_nonnegative(gc, engine):
     for n in (0, 1, 4, 16):
         o = gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=n, sweeps_per_relabel=4,
                          engine=engine)
-        X, flow, status, _ = _solve_costs(gc, C, wl.lam, wl.inhibit, 1, o)
+        X, flow, status, _ = _solve_costs(gc, C, wl.lam, wl.inhibit, 1, o, direction)
         assert status == gc.GS_OK
         E = oracle.energy(C, X, wl.lam, wl.inhibit, 1)
         assert flow <= ref["flow"] <= E          # weak duality on both sides
