@@ -321,8 +321,14 @@ def run(args):
     wl = _workload()
     p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
                   vertical_inhibit=1)
-    o = gc.SolveOpts(sweeps_per_relabel=args.sweeps_per_relabel, local_iters=args.local_iters,
-                     relabel_passes=args.relabel_passes)
+    from paper_1803_01516_gb300 import autotune
+    o = autotune.tuned_opts(p)               # tile shape and schedule for this size bucket
+    if args.sweeps_per_relabel:
+        o.sweeps_per_relabel = args.sweeps_per_relabel
+    if args.local_iters:
+        o.local_iters = args.local_iters
+    if args.relabel_passes:
+        o.relabel_passes = args.relabel_passes
     # each rank solves its own pairs (replicas)
     pairs = [synth.make_pair(wl, i) for i in replica_pairs(rank)]
     Ld = [torch.from_numpy(L).to(dev) for L, _, _ in pairs]
@@ -454,7 +460,8 @@ def run(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": _config(wl, {"sweeps_per_relabel": o.sweeps_per_relabel,
                                "local_iters": o.local_iters, "relabel_passes": o.relabel_passes,
-                               "replicas": world, "tile": [ti["tile_w"], ti["tile_h"]]}),
+                               "replicas": world, "tile": [ti["tile_w"], ti["tile_h"]],
+                               "direction": "auto"}),
         "e2e": e2e,
         "roofline": {"bound": "hbm", "kernel": "k_batch (max-flow)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -489,9 +496,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gazecut", choices=["gazecut", "reference"])
-    ap.add_argument("--sweeps-per-relabel", type=int, default=16)
-    ap.add_argument("--local-iters", type=int, default=8)
-    ap.add_argument("--relabel-passes", type=int, default=8)
+    ap.add_argument("--sweeps-per-relabel", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--local-iters", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--relabel-passes", type=int, default=0, help="0: autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=64)
