@@ -53,6 +53,7 @@ struct SolveArgs {
     int32_t *tile_act;   // [2][T] tiles with work in the current / next sweep round
     int32_t *tile_dirty; // [2][T] tiles whose halo heights changed in the last relabel pass
     int32_t *tile_cnt;   // [T] active nodes per tile after its last relabel pass
+    int32_t *tile_list;  // [3][T] tiles queued for a step (slot = step mod 3)
     int32_t *hgt;        // distances the relabel passes compute (state heights, or marks)
     int dir;             // 0: distance to sink capacity over out-arcs (heights);
                          // 1: distance from positive excess over in-arcs (reachability);
@@ -500,12 +501,28 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
     return tot;
 }
 
+// Queue a tile for the next step, once: the caller that turns its flag from 0
+// to 1 appends it to the list, and the tile's visit in that step clears the
+// flag again.
+__device__ __forceinline__ void enqueue(int32_t *flag, int32_t *list, int32_t *count, int tile) {
+    if (atomicExch(&flag[tile], 1) == 0) __stcg(&list[atomicAdd(count, 1)], tile);
+}
+
+// Neighbour tile on side q (0: W-1, 1: W+1, 2: y-1, 3: y+1), or -1.
+__device__ __forceinline__ int side_tile(const TileGeom &t, const TileOrigin &o, int tile, int q) {
+    if (q == 0) return o.tx > 0 ? tile - 1 : -1;
+    if (q == 1) return o.tx + 1 < t.tiles_w ? tile + 1 : -1;
+    if (q == 2) return o.ty > 0 ? tile - t.tiles_w : -1;
+    return o.ty + 1 < t.tiles_h ? tile + t.tiles_w : -1;
+}
+
 // Later relabel passes: masks from the first pass, heights from global
 // memory (own and halo); relax, write back what changed, mark the neighbour
 // tiles whose halo changed, and return the change of the tile's active count.
 template <int NPT>
 __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, int tile,
-                                       int &changed, int32_t *dirty_next) {
+                                       int &changed, int32_t *dirty_next, int32_t *list_next,
+                                       int32_t *count_next) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const State &s = a.s;
@@ -558,12 +575,9 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
     }
     if (sides) atomicOr(&s_sides, (int)sides);
     const long long tot = block_sum(act);   // also orders s_sides
-    if (threadIdx.x == 0) {
-        const unsigned sd = (unsigned)s_sides;
-        if ((sd & 1u) && o.tx > 0) __stcg(&dirty_next[tile - 1], 1);
-        if ((sd & 2u) && o.tx + 1 < t.tiles_w) __stcg(&dirty_next[tile + 1], 1);
-        if ((sd & 4u) && o.ty > 0) __stcg(&dirty_next[tile - t.tiles_w], 1);
-        if ((sd & 8u) && o.ty + 1 < t.tiles_h) __stcg(&dirty_next[tile + t.tiles_w], 1);
+    if (threadIdx.x < 4 && ((unsigned)s_sides >> threadIdx.x & 1u)) {
+        const int nb = side_tile(t, o, tile, threadIdx.x);
+        if (nb >= 0) enqueue(dirty_next, list_next, count_next, nb);
     }
     if (ch) changed = 1;
     const long long before = ld(&a.tile_cnt[tile]);
@@ -577,7 +591,7 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
 // Up to local_iters push/relabel iterations of one tile in shared memory.
 template <int NPT>
 __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round, int iters,
-                           int &overflow) {
+                           int &overflow, int32_t *list_next, int32_t *count_next) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const State &s = a.s;
@@ -743,26 +757,30 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
                            ((unsigned)__syncthreads_or((int)(nb_touch & 2u)) << 1) |
                            ((unsigned)__syncthreads_or((int)(nb_touch & 4u)) << 2) |
                            ((unsigned)__syncthreads_or((int)(nb_touch & 8u)) << 3);
-    if (threadIdx.x == 0) {
-        if (still_any) __stcg(&act_next[tile], 1);
-        if ((touch & 1u) && o.tx > 0) __stcg(&act_next[tile - 1], 1);
-        if ((touch & 2u) && o.tx + 1 < t.tiles_w) __stcg(&act_next[tile + 1], 1);
-        if ((touch & 4u) && o.ty > 0) __stcg(&act_next[tile - t.tiles_w], 1);
-        if ((touch & 8u) && o.ty + 1 < t.tiles_h) __stcg(&act_next[tile + t.tiles_w], 1);
+    if (threadIdx.x < 4 && (touch >> threadIdx.x & 1u)) {
+        const int nb = side_tile(t, o, tile, threadIdx.x);
+        if (nb >= 0) enqueue(act_next, list_next, count_next, nb);
     }
+    if (threadIdx.x == 4 && still_any) enqueue(act_next, list_next, count_next, tile);
     __syncthreads();
 }
 
 // ------------------------------------------------------- the solve loop ---
 //
-// One cooperative launch solves n independent pairs.  The grid walks the
-// concatenated tiles of all pairs in steps separated by grid barriers; in a
-// step every tile does the work of its pair's current phase:
+// One cooperative launch solves n independent pairs in steps separated by
+// grid barriers; in a step each pair's tiles with work do its current phase:
 //
 //   INIT   first relabel pass (masks, heights reset, in-tile distances)
 //   PASS   later relabel pass (all tiles once, then tiles whose halo changed)
 //   SWEEP  one sweep round over the tiles with work
 //   DONE   nothing
+//
+// A step's work items are the pairs' segments laid end to end: all T tiles of
+// a pair in INIT, its first PASS, its first SWEEP round (those with active
+// nodes) or LABELS; otherwise the tiles queued for this step by the visits of
+// the step before.  Blocks claim items one at a time from a counter, so a step
+// ends when the items run out, not when the block with the most tiles of a
+// fixed share finishes.
 //
 // After each barrier every block advances every pair's state machine from the
 // same per-pair sums (so all blocks take the same decisions) -- a pair that is
@@ -791,6 +809,8 @@ struct BatchArgs {
     int tile_off[kMaxPairs + 1];
     Ctrl *bar;        // grid barrier and abort flag
     long long *red;   // per-step, per-pair sums [3][n][4]
+    int32_t *claim;   // per-step claim counters [3]
+    int32_t *qcount;  // per-step, per-pair lengths of the tile queues [3][kMaxPairs]
     SolveArgs pair[kMaxPairs];
 };
 
@@ -949,11 +969,40 @@ __device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
     return block_sum((long long)deficit);
 }
 
+// Phases whose work items this step are the tiles queued by the step before.
+__device__ __forceinline__ bool queued(const PairState &st) {
+    return (st.phase == PH_PASS && st.pass > 1) || (st.phase == PH_SWEEP && st.round > 0);
+}
+
+// Claim this step's next work item (thread 0): the global tile index, or -1
+// when the items have run out.  A first sweep round skips tiles whose last
+// relabel pass left no active node.
+__device__ int claim_item(const BatchArgs &B, const PairState *S, const int *seg, int slot) {
+    const int V = seg[B.n];
+    for (;;) {
+        const int v = atomicAdd(&B.claim[slot], 1);
+        if (v >= V) return -1;
+        int lo = 0, hi = B.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        const SolveArgs &a = B.pair[lo];
+        const int idx = v - seg[lo];
+        int tile = idx;
+        if (queued(S[lo])) tile = ld(&a.tile_list[slot * a.t.T + idx]);
+        else if (S[lo].phase == PH_SWEEP && ld(&a.tile_cnt[tile]) <= 0) continue;
+        return B.tile_off[lo] + tile;
+    }
+}
+
 template <int NPT>
 __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant__ BatchArgs B) {
     extern __shared__ int32_t smem[];
     __shared__ PairState S[kMaxPairs];
-    __shared__ int s_work, s_all_done;
+    __shared__ int s_seg[kMaxPairs + 1];   // this step's work items: prefix offsets per pair
+    __shared__ int s_claim[2];
     for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
         PairState st;
         memset(&st, 0, sizeof(st));
@@ -965,15 +1014,31 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
     __syncthreads();
     unsigned long long t_step = now_ns();
     for (long long step = 0;; step++) {
-        long long *red = B.red + (step % 3) * B.n * 4;
-        for (int gt = blockIdx.x; gt < B.T_total; gt += gridDim.x) {
+        const int slot = (int)(step % 3), next = (int)((step + 1) % 3);
+        long long *red = B.red + slot * B.n * 4;
+        // work items per pair, then their prefix offsets
+        for (int p = threadIdx.x; p < B.n; p += blockDim.x)
+            s_seg[p + 1] = queued(S[p]) ? *(volatile int32_t *)&B.qcount[slot * kMaxPairs + p]
+                                        : (S[p].phase == PH_DONE ? 0 : B.pair[p].t.T);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_seg[0] = 0;
+            for (int p = 0; p < B.n; p++) s_seg[p + 1] += s_seg[p];
+        }
+        __syncthreads();
+        for (int it = 0;; it++) {
+            if (threadIdx.x == 0) s_claim[it & 1] = claim_item(B, S, s_seg, slot);
+            __syncthreads();
+            const int gt = s_claim[it & 1];
+            if (gt < 0) break;
             const int pr = pair_of(B, gt);
             const int tile = gt - B.tile_off[pr];
             const SolveArgs &a = B.pair[pr];
             const int phase = S[pr].phase;
-            if (phase == PH_DONE) continue;
             const TileSmem m = tile_smem(smem, a.t.PN);
             const int T = a.t.T;
+            int32_t *list_next = a.tile_list + next * T;
+            int32_t *count_next = B.qcount + next * kMaxPairs + pr;
             long long va = 0, vb = 0, vc = 0;
             int ovf = 0;
             if (phase == PH_INIT) {
@@ -982,33 +1047,23 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                 if (threadIdx.x == 0) {
                     __stcg(&a.tile_dirty[tile], 0);
                     __stcg(&a.tile_dirty[T + tile], 0);
+                    __stcg(&a.tile_act[tile], 0);
                     __stcg(&a.tile_act[T + tile], 0);
                 }
             } else if (phase == PH_PASS) {
                 const int pass = S[pr].pass;
                 int32_t *dcur = a.tile_dirty + (pass & 1) * T;
                 int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
-                if (pass > 1) {
-                    __syncthreads();
-                    if (threadIdx.x == 0) s_work = ld(&dcur[tile]);
-                    __syncthreads();
-                    if (!s_work) continue;
-                    if (threadIdx.x == 0) __stcg(&dcur[tile], 0);
-                }
+                if (pass > 1 && threadIdx.x == 0) __stcg(&dcur[tile], 0);
                 int ch = 0;
-                va = relabel_pass_tile<NPT>(a, m, tile, ch, dnext);
+                va = relabel_pass_tile<NPT>(a, m, tile, ch, dnext, list_next, count_next);
                 vb = ch;
                 vc = 1;
             } else if (phase == PH_SWEEP) {
-                const long long r = S[pr].round;
-                const int cur = (int)(r & 1);
-                __syncthreads();
-                if (threadIdx.x == 0)
-                    s_work = r == 0 ? (ld(&a.tile_cnt[tile]) > 0) : ld(&a.tile_act[cur * T + tile]);
-                __syncthreads();
+                const int cur = (int)(S[pr].round & 1);
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
-                if (!s_work) continue;
-                sweep_tile<NPT>(a, m, tile, cur, S[pr].tail ? a.tail_iters : a.local_iters, ovf);
+                sweep_tile<NPT>(a, m, tile, cur, S[pr].tail ? a.tail_iters : a.local_iters, ovf,
+                                list_next, count_next);
                 ovf = __syncthreads_or(ovf);
                 va = 1;
             } else {   // PH_LABELS
@@ -1024,11 +1079,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                 if (ovf) atomicAdd((unsigned long long *)&rp[3], 1ull);
             }
         }
-        // the sums of step + 1 start from zero (their slot was last read two
-        // barriers ago)
-        if (blockIdx.x == 0)
+        // the sums and the claim counter of step + 1 start from zero (their
+        // slots were last used two steps ago); so do the queues that step + 1
+        // fills for step + 2 (last read at the start of the step before this)
+        if (blockIdx.x == 0) {
             for (int i = threadIdx.x; i < B.n * 4; i += blockDim.x)
-                B.red[((step + 1) % 3) * B.n * 4 + i] = 0;
+                B.red[next * B.n * 4 + i] = 0;
+            for (int i = threadIdx.x; i < B.n; i += blockDim.x)
+                B.qcount[((step + 2) % 3) * kMaxPairs + i] = 0;
+            if (threadIdx.x == 0) B.claim[next] = 0;
+        }
         grid_sync_sum(B.bar, 0);
         if (aborted(B.bar)) break;
         int done = 1;
@@ -1126,7 +1186,7 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
 static int64_t max_tiles(const Geom &g) { return (int64_t)((g.ng + 3) / 4) * g.h; }
 
 size_t tiled_work_extra(const Geom &g) {
-    return round_up(g.N * sizeof(uint16_t), 256) + round_up(5 * max_tiles(g) * sizeof(int32_t), 256);
+    return round_up(g.N * sizeof(uint16_t), 256) + round_up(8 * max_tiles(g) * sizeof(int32_t), 256);
 }
 
 // Per-pair arguments from the pair's geometry, state and workspace.
@@ -1141,6 +1201,7 @@ static int setup_args(const Geom &g, const State &s, const Work &w, const gs_sol
     a.tile_act = (int32_t *)(extra + round_up(g.N * sizeof(uint16_t), 256));
     a.tile_dirty = a.tile_act + 2 * a.t.T;
     a.tile_cnt = a.tile_act + 4 * a.t.T;
+    a.tile_list = a.tile_act + 5 * a.t.T;
     a.ctrl = w.ctrl;
     return GS_OK;
 }
@@ -1187,12 +1248,17 @@ static int launch_batch(const BatchArgs &B, int npt, size_t smem, cudaStream_t s
     return GS_OK;
 }
 
-// Control words of a batch launch: the barrier block, then the per-step sums.
-constexpr size_t kBatchCtrlBytes = 256 + 3 * kMaxPairs * 4 * sizeof(long long);
+// Control words of a batch launch: the barrier block, the per-step sums, the
+// claim counters and the queue lengths.
+constexpr size_t kBatchRedBytes = 3 * kMaxPairs * 4 * sizeof(long long);
+constexpr size_t kBatchCtrlBytes = 256 + kBatchRedBytes + 16 + 3 * kMaxPairs * sizeof(int32_t);
+static_assert(256 + kBatchCtrlBytes <= kWorkCtrlBytes, "a pair's workspace holds a batch's control");
 
 static int run_batch(BatchArgs &B, int npt, size_t smem, void *ctrl_mem, cudaStream_t st) {
     B.bar = (Ctrl *)ctrl_mem;
     B.red = (long long *)((char *)ctrl_mem + 256);
+    B.claim = (int32_t *)((char *)ctrl_mem + 256 + kBatchRedBytes);
+    B.qcount = B.claim + 4;
     int total = 0;
     for (int p = 0; p < B.n; p++) {
         B.tile_off[p] = total;
@@ -1200,7 +1266,7 @@ static int run_batch(BatchArgs &B, int npt, size_t smem, void *ctrl_mem, cudaStr
     }
     B.tile_off[B.n] = total;
     B.T_total = total;
-    GS_CUDA_TRY(cudaMemsetAsync(ctrl_mem, 0, 256 + 3 * (size_t)B.n * 4 * sizeof(long long), st));
+    GS_CUDA_TRY(cudaMemsetAsync(ctrl_mem, 0, kBatchCtrlBytes, st));
     return launch_batch(B, npt, smem, st);
 }
 
