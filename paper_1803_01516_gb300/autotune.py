@@ -23,7 +23,7 @@ import torch
 from . import gazecut as gc
 from . import synth
 
-SCHEDULES = [(spr, li, rp) for spr in (8, 16, 32) for li in (8, 16) for rp in (4, 8, 16)]
+SCHEDULES = [(spr, li, rp) for spr in (8, 16, 32, 64) for li in (4, 8, 16) for rp in (4, 8, 16)]
 SHAPES = [(16, 8), (8, 8), (16, 4), (32, 4), (8, 4), (16, 2), (8, 2), (4, 4)]
 
 
