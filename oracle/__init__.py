@@ -13,8 +13,12 @@ Functions (citations are to the paper):
                     returns flow, canonical labels X_min (smallest minimiser,
                     from S_min), the cut capacity of S_min and X_max
 * ``energy``        E(X) = Σ g_v(X_v) + Σ h~(X_u - X_v), §2 and §3
+* ``solve_band``    exact min of E(X) under per-site bounds lo <= X <= hi
+                    (the second cut of the level-1 approximation, §4.5)
 * ``small.brute_force`` / ``small.viterbi_row``  enumeration and the textbook
                     chain DP that pin ``solve`` (see ``small.py``)
+* ``level1.level1`` the level-1 hierarchical approximation of §4.5 (delegate
+                    points, first cut, thin skin, second cut; module ``level1``)
 """
 from __future__ import annotations
 
@@ -53,6 +57,8 @@ def _load():
         lib.or_energy.restype = ctypes.c_int64
         lib.or_solve.argtypes = [P, I, I, I, I, I, I, I, P, P, P, P]
         lib.or_solve.restype = I
+        lib.or_solve_band.argtypes = [P, I, I, I, I, I, I, P, P, I, P, P]
+        lib.or_solve_band.restype = I
         lib.or_graph_size.argtypes = [I, I, I, I, P, P]
         lib.or_graph_size.restype = None
         _lib = lib
@@ -101,6 +107,26 @@ def solve(C: np.ndarray, lam: int, inhibit: int, vinhibit: int = 1, method: str 
     if rc:
         raise RuntimeError(f"or_solve failed (rc={rc})")
     return {"flow": int(flow[0]), "labels": X, "cut": int(cut[0]), "labels_max": Xmax}
+
+
+def solve_band(C: np.ndarray, lam: int, inhibit: int, vinhibit: int, lo: np.ndarray,
+               hi: np.ndarray, method: str = "bk"):
+    """Exact minimiser of E(X) subject to lo <= X <= hi (int32 [h, n_g] each).
+    Returns dict(flow, labels): the canonical smallest minimiser of the
+    restricted problem and its energy (= the flow of the pinned graph)."""
+    lib = _load()
+    C = np.ascontiguousarray(C, dtype=np.int32)
+    h, ng, D = C.shape
+    lo = np.ascontiguousarray(lo, dtype=np.int32)
+    hi = np.ascontiguousarray(hi, dtype=np.int32)
+    assert lo.shape == (h, ng) and hi.shape == (h, ng)
+    X = np.zeros((h, ng), dtype=np.int32)
+    flow = np.zeros(1, dtype=np.int64)
+    rc = lib.or_solve_band(_ptr(C), ng, h, D, lam, inhibit, vinhibit, _ptr(lo), _ptr(hi),
+                           0 if method == "bk" else 1, _ptr(flow), _ptr(X))
+    if rc:
+        raise RuntimeError(f"or_solve_band failed (rc={rc})")
+    return {"flow": int(flow[0]), "labels": X}
 
 
 def graph_size(ng: int, h: int, D: int, vinhibit: int = 1):

@@ -138,15 +138,15 @@ static int node_id(int ng, int D, int W, int y, int k)
  * For labels a = X_u, b = X_v the cut penalty arcs number |a-b| and the cut
  * inhibit arcs (|a-b|-1)_+, which reproduces h~ of §3 exactly. */
 static int build(graph_t *g, const int32_t *C, int ng, int h, int D, int lam, int inhibit,
-                 int vinhibit)
+                 int vinhibit, long long extra)
 {
     long long sites = (long long)ng * h;
     long long hp = (long long)(ng - 1) * h, vp = (long long)ng * (h - 1);
     long long ip = inhibit > 0 ? hp + (vinhibit ? vp : 0) : 0;
     long long edges = sites * D + (hp + vp) * (D - 1) + 2 * ip * (D > 2 ? D - 2 : 0);
     long long n = 2 + sites * (D - 1);
-    if (n > 2000000000LL || 2 * edges > 2000000000LL) return 2;
-    if (g_init(g, (int)n, (int)(2 * edges))) return 3;
+    if (n > 2000000000LL || 2 * (edges + extra) > 2000000000LL) return 2;
+    if (g_init(g, (int)n, (int)(2 * (edges + extra)))) return 3;
     for (int y = 0; y < h; y++)
         for (int W = 0; W < ng; W++) {
             const int32_t *c = C + ((size_t)y * ng + W) * D;
@@ -469,7 +469,7 @@ int or_solve(const int32_t *C, int ng, int h, int D, int lam, int inhibit, int v
     if (D < 2 || ng < 1 || h < 1 || lam < 0 || inhibit < 0) return 1;
     for (size_t i = 0; i < (size_t)ng * h * D; i++) if (C[i] < 0) return 1;
     graph_t g;
-    int rc = build(&g, C, ng, h, D, lam, inhibit, vinhibit);
+    int rc = build(&g, C, ng, h, D, lam, inhibit, vinhibit, 0);
     if (rc) { g_free(&g); return 10 + rc; }
     i64 flow = method == 0 ? bk_maxflow(&g) : dinic_maxflow(&g);
     unsigned char *inS = (unsigned char *)malloc((size_t)g.n);
@@ -507,6 +507,52 @@ int or_solve(const int32_t *C, int ng, int h, int D, int lam, int inhibit, int v
             labels_max[v] = a;
         }
         free(inT); free(queue);
+    }
+    free(inS);
+    g_free(&g);
+    return bad ? 6 : 0;
+}
+
+/*
+ * The second cut of the level-1 approximation (§4.5): the exact minimum of
+ * E(X) over labelings with lo_v <= X_v <= hi_v at every site (the "thin skin"
+ * around the first cut).  The bounds pin chain nodes to a side: X_v >= lo_v
+ * puts n(v,1..lo_v) on the source side (an infinite arc s -> n(v,lo_v); the
+ * infinite reverse chain arcs carry it down the chain), X_v <= hi_v puts
+ * n(v,hi_v+1..D-1) on the sink side (an infinite arc n(v,hi_v+1) -> t).
+ * lo, hi: int32 [h][n_g], 0 <= lo <= hi <= D-1.  Outputs as or_solve (the
+ * flow value is that of the pinned graph, i.e. E of the labels).  Returns 1 on
+ * bad bounds, else as or_solve.
+ */
+int or_solve_band(const int32_t *C, int ng, int h, int D, int lam, int inhibit, int vinhibit,
+                  const int32_t *lo, const int32_t *hi, int method, i64 *flow_out,
+                  int32_t *labels)
+{
+    if (D < 2 || ng < 1 || h < 1 || lam < 0 || inhibit < 0) return 1;
+    for (size_t i = 0; i < (size_t)ng * h * D; i++) if (C[i] < 0) return 1;
+    for (size_t v = 0; v < (size_t)ng * h; v++)
+        if (lo[v] < 0 || lo[v] > hi[v] || hi[v] > D - 1) return 1;
+    graph_t g;
+    int rc = build(&g, C, ng, h, D, lam, inhibit, vinhibit, 2LL * ng * h);
+    if (rc) { g_free(&g); return 10 + rc; }
+    for (int y = 0; y < h; y++)
+        for (int W = 0; W < ng; W++) {
+            size_t v = (size_t)y * ng + W;
+            if (lo[v] >= 1) g_edge(&g, SRC, node_id(ng, D, W, y, lo[v]), OR_INF, 0);
+            if (hi[v] <= D - 2) g_edge(&g, node_id(ng, D, W, y, hi[v] + 1), SNK, OR_INF, 0);
+        }
+    i64 flow = method == 0 ? bk_maxflow(&g) : dinic_maxflow(&g);
+    unsigned char *inS = (unsigned char *)malloc((size_t)g.n);
+    reach_from_source(&g, inS);
+    if (inS[SNK]) { free(inS); g_free(&g); return 5; }
+    *flow_out = flow;
+    int bad = 0;
+    for (size_t v = 0; v < (size_t)ng * h; v++) {
+        int W = (int)(v % ng), y = (int)(v / ng);
+        int a = 0;
+        while (a + 1 <= D - 1 && inS[node_id(ng, D, W, y, a + 1)]) a++;
+        for (int k = a + 1; k <= D - 1; k++) if (inS[node_id(ng, D, W, y, k)]) bad = 1;
+        labels[v] = a;
     }
     free(inS);
     g_free(&g);

@@ -4,6 +4,8 @@
                     many labelings at once.
 * ``brute_force``   every labeling of a tiny grid (D^n of them): the exact
                     minimum and the component-wise smallest minimiser.
+* ``brute_force_band``  every labeling inside per-site bounds lo <= X <= hi:
+                    the restricted minimum and its smallest minimiser.
 * ``viterbi_row``   one row of sites with no vertical pairs is a chain MRF;
                     min-sum dynamic programming gives its exact minimum, and
                     forward + backward messages give, per site, the smallest
@@ -41,6 +43,22 @@ def brute_force(C: np.ndarray, lam: int, inhibit: int, vinhibit: int = 1):
     n = h * ng
     assert D ** n <= 2_000_000, "too many labelings"
     allX = np.array(list(itertools.product(range(D), repeat=n)), dtype=np.int64).reshape(-1, h, ng)
+    E = energy_np(C, allX, lam, inhibit, vinhibit)
+    Emin = int(E.min())
+    mins = allX[E == Emin]
+    return Emin, mins.min(axis=0).astype(np.int32), int(mins.shape[0])
+
+
+def brute_force_band(C: np.ndarray, lam: int, inhibit: int, vinhibit: int, lo: np.ndarray,
+                     hi: np.ndarray):
+    """Exhaustive minimum over labelings with lo <= X <= hi.  Returns
+    (E*, X_min, n_minimisers) of the restricted problem."""
+    C = np.asarray(C, dtype=np.int64)
+    h, ng, D = C.shape
+    ranges = [range(int(a), int(b) + 1) for a, b in zip(np.ravel(lo), np.ravel(hi))]
+    count = int(np.prod([len(r) for r in ranges]))
+    assert count <= 2_000_000, "too many labelings"
+    allX = np.array(list(itertools.product(*ranges)), dtype=np.int64).reshape(-1, h, ng)
     E = energy_np(C, allX, lam, inhibit, vinhibit)
     Emin = int(E.min())
     mins = allX[E == Emin]
