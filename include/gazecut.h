@@ -255,6 +255,66 @@ GS_API size_t gs_batch_workspace_bytes(int32_t n);
 GS_API int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batch_workspace,
                             void *stream);
 
+/*
+ * Level-1 hierarchical approximation (§4.5).  The paper combines b x b x b
+ * neighbouring cross points into a delegate point, cuts the delegate graph,
+ * then cuts exactly among the cross points of a thin skin around that cut.
+ * It leaves the delegate terms and the skin open; this library fixes them:
+ *
+ *   delegate site (Wc, yc) = sites W in [b Wc, b Wc + b), y in [b yc, b yc + b)
+ *   delegate depth number Lc = depth numbers [b Lc, b Lc + b)   (fewer at the
+ *     far edges); n_gc = ceil(n_g / b), h_c = ceil(h / b), D_c = ceil(D / b)
+ *   delegate data term  Cc(Wc, yc, Lc) = sum over the block's sites of the
+ *     smallest data term in the depth bin
+ *   delegate interaction  h~ of §3 with lambda and inhibit multiplied by b
+ *   thin skin  a site whose delegate has label Lc keeps the depth numbers
+ *     [b Lc - b, b Lc + 2b - 1] clipped to [0, D-1]
+ *   second cut  the exact minimum of E (§2) over labelings inside the skin;
+ *     its canonical (smallest) minimiser
+ *
+ * b = 1 gives the exact cut.  A caller runs: gs_delegate_params,
+ * gs_delegate_cost, the exact path on the delegate problem (gs_build_graph,
+ * gs_maxflow_solve, gs_extract_labels), gs_skin_bounds on the delegate labels,
+ * gs_build_graph_skin, then gs_maxflow_solve and gs_extract_labels with the
+ * fine params.
+ */
+
+/* Params of the delegate problem for block size b (host; 1 <= b < D):
+ * w = n_gc + dis0_c, h = h_c, D = D_c, dis0 = 2 (D_c - 1), lambda and inhibit
+ * times b, the rest copied.  GS_ERR_INVAL for bad params or b, GS_ERR_OVERFLOW
+ * when the scaled weights leave their range. */
+GS_API int gs_delegate_params(const gs_params *p, int32_t b, gs_params *out);
+
+/* Delegate data term: coarse[(yc*n_gc + Wc)*D_c + Lc] (int32, layout of a cost
+ * volume of the delegate problem) from cost (layout of gs_stereo_cost_volume).
+ * status: device int32[1], set to GS_OK, GS_ERR_INVAL (a negative cost) or
+ * GS_ERR_OVERFLOW (a delegate term above 2^30). */
+GS_API int gs_delegate_cost(const int32_t *cost, const gs_params *p, int32_t b, int32_t *coarse,
+                            int32_t *status, void *stream);
+
+/* Skin bounds lo, hi (int32 [h][n_g] each, device) from the delegate labels
+ * (int32 [h_c][n_gc], device).  status: device int32[1], GS_ERR_LABELS when a
+ * delegate label is outside [0, D_c), else left as is. */
+GS_API int gs_skin_bounds(const int32_t *coarse_labels, const gs_params *p, int32_t b, int32_t *lo,
+                          int32_t *hi, int32_t *status, void *stream);
+
+/*
+ * Graph of the second cut: the chain graph of gs_build_graph for the problem
+ * as given (p->direction is ignored; the label-reversed twin is never taken)
+ * with every site's labels held in [lo, hi] (int32 [h][n_g] each, device,
+ * 0 <= lo <= hi <= D-1).  X >= lo keeps n_1..n_lo on the source side: n_lo gets
+ * extra source capacity one above everything that can leave that set (the
+ * data arc at lo and the penalty and inhibit arcs into neighbours' nodes that
+ * are not held to the source side), so no cut that cuts it can be minimal; X
+ * <= hi holds n_hi+1.. on the sink side the same way with extra sink
+ * capacity.  The flow value gs_extract_labels reports for this graph includes
+ * these capacities; the energy of the labels (gs_energy) is the restricted
+ * minimum.  status as gs_build_graph, plus GS_ERR_INVAL for bounds out of
+ * order.
+ */
+GS_API int gs_build_graph_skin(const int32_t *cost, const gs_params *p, const int32_t *lo,
+                               const int32_t *hi, void *graph, int32_t *status, void *stream);
+
 /* Tile shape the TILED engine uses for these params and options: host
  * int32[4] = {sites per tile along W, rows per tile, number of tiles, shared
  * bytes}.  GS_ERR_INVAL if the requested shape does not fit. */

@@ -120,6 +120,73 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
     block_sum_u64(src, &s.hdr->src_total);
 }
 
+// Skin bounds of the level-1 second cut (§4.5), one thread per site.  The
+// set n_1..n_lo of a site with lo >= 1 is held on the source side by extra
+// source capacity at n_lo: one above the capacity of every arc that leaves the
+// set for a node not held there, i.e. the data arc at lo (C(lo)), the penalty
+// arcs v_k -> u_k with lo_u < k <= lo ((lo - lo_u)_+ of them) and the inhibit
+// arcs v_k -> u_(k-1) with lo_u + 1 < k <= lo ((lo - lo_u - 1)_+).  A cut that
+// left part of the set on the sink side would pay that extra arc; moving every
+// such set back to the source side saves it and adds less than it, so a
+// minimum cut keeps the bounds.  n_hi+1..n_(D-1) is held on the sink side by
+// extra sink capacity (a deficit) at n_hi+1, counted over the arcs that enter
+// the set the same way.  Totals join the header sums that the overflow check
+// and the flow value use.
+__global__ void k_skin(const int32_t *__restrict__ C, const int32_t *__restrict__ lo,
+                       const int32_t *__restrict__ hi, Geom g, State s, int32_t *status) {
+    unsigned long long src = 0, dfc = 0;
+    int bad = 0, big = 0;
+    const int64_t sites = (int64_t)g.ng * g.h;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < sites;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int W = (int)(v % g.ng), y = (int)(v / g.ng);
+        const int a = lo[v], b = hi[v];
+        if (a < 0 || a > b || b > g.D - 1) {
+            bad = 1;
+            continue;
+        }
+        const int32_t *cs = C + v * g.D;
+        const int64_t nb[4] = {W > 0 ? v - 1 : -1, W + 1 < g.ng ? v + 1 : -1,
+                               y > 0 ? v - g.ng : -1, y + 1 < g.h ? v + g.ng : -1};
+        if (a >= 1) {
+            long long x = (long long)cs[a] + 1;
+            for (int q = 0; q < 4; q++) {
+                if (nb[q] < 0) continue;
+                const long long d = a - lo[nb[q]];
+                const long long h2 = q < 2 ? g.h2h : g.h2v;
+                x += (long long)g.lam * max(d, 0ll) + h2 * max(d - 1, 0ll);
+            }
+            big |= x > kCapLimit;
+            x = min(x, (long long)kCapLimit);
+            const int64_t i = ((int64_t)y * g.K + (a - 1)) * g.P + W;
+            s.ex[i] += (int32_t)x;
+            src += (unsigned long long)x;
+        }
+        if (b <= g.D - 2) {
+            long long x = (long long)cs[b] + 1;
+            for (int q = 0; q < 4; q++) {
+                if (nb[q] < 0) continue;
+                const long long d = hi[nb[q]] - b;
+                const long long h2 = q < 2 ? g.h2h : g.h2v;
+                x += (long long)g.lam * max(d, 0ll) + h2 * max(d - 1, 0ll);
+            }
+            big |= x > kCapLimit;
+            x = min(x, (long long)kCapLimit);
+            const int64_t i = ((int64_t)y * g.K + b) * g.P + W;
+            s.ex[i] -= (int32_t)x;
+            dfc += (unsigned long long)x;
+        }
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_INVAL);
+    }
+    if (__syncthreads_or(big)) {
+        if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_OVERFLOW);
+    }
+    block_sum_u64(src, &s.hdr->src_total);
+    block_sum_u64(dfc, &s.hdr->init_deficit);
+}
+
 __global__ void k_check_totals(const GraphHeader *hdr, int32_t *status) {
     if (hdr->src_total > (unsigned long long)kCapLimit ||
         hdr->init_deficit > (unsigned long long)kCapLimit)
@@ -232,6 +299,25 @@ int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t
     k_dir_sums<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(cost, g, s.hdr);
     k_decide<<<1, 1, 0, st>>>(s.hdr, p->direction);
     k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
+    k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
+    count_launches(5);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_build_graph_skin(const int32_t *cost, const gs_params *p, const int32_t *lo,
+                        const int32_t *hi, void *graph, int32_t *status, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !cost || !lo || !hi || !graph || !status)
+        return GS_ERR_INVAL;
+    if (((uintptr_t)graph & 255) != 0) return GS_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    State s = state_view(graph, g);
+    GS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    k_header<<<1, 1, 0, st>>>(s.hdr, g, p->inhibit, p->vertical_inhibit);
+    k_decide<<<1, 1, 0, st>>>(s.hdr, 1);
+    k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
+    k_skin<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(cost, lo, hi, g, s, status);
     k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
     count_launches(5);
     GS_CUDA_TRY(cudaGetLastError());

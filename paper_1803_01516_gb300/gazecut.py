@@ -32,6 +32,7 @@ EXPORTS = [
     "gs_noalloc_scratch_bytes", "gs_maxflow_solve_noalloc", "gs_tile_info",
     "gs_stereo_cost_volume_f32", "gs_energy_backward", "gs_cost_volume_f32_backward",
     "gs_cost_add_at_labels", "gs_batch_workspace_bytes", "gs_solve_batched",
+    "gs_delegate_params", "gs_delegate_cost", "gs_skin_bounds", "gs_build_graph_skin",
 ]
 
 
@@ -138,6 +139,10 @@ def lib():
             "gs_cost_add_at_labels": ([P, P, pp, I32, P], ctypes.c_int),
             "gs_batch_workspace_bytes": ([I32], SZ),
             "gs_solve_batched": ([P, I32, P, P], ctypes.c_int),
+            "gs_delegate_params": ([pp, I32, pp], ctypes.c_int),
+            "gs_delegate_cost": ([P, pp, I32, P, P, P], ctypes.c_int),
+            "gs_skin_bounds": ([P, pp, I32, P, P, P, P], ctypes.c_int),
+            "gs_build_graph_skin": ([P, pp, P, P, P, P, P], ctypes.c_int),
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -308,6 +313,52 @@ def gs_maxflow_solve_noalloc(graph: torch.Tensor, p: Params, o: SolveOpts, statu
                                           _stream(stream))
 
 
+# ------------------------------------------------ level-1 approximation ---
+
+def gs_delegate_params(p: Params, b: int) -> Params:
+    """Params of the delegate problem for block size b (§4.5)."""
+    out = GsParams()
+    _check(lib().gs_delegate_params(ctypes.byref(p.c()), int(b), ctypes.byref(out)),
+           "gs_delegate_params")
+    return Params(w=out.w, h=out.h, D=out.D, tau=out.tau, lam=out.lambda_, inhibit=out.inhibit,
+                  vertical_inhibit=out.vertical_inhibit, dis0=out.dis0, direction=out.direction)
+
+
+def gs_delegate_cost(cost: torch.Tensor, p: Params, b: int, coarse: torch.Tensor,
+                     status: torch.Tensor, stream=None):
+    pc = gs_delegate_params(p, b)
+    if cost.numel() * 4 != gs_cost_volume_bytes(p) or coarse.numel() * 4 != gs_cost_volume_bytes(pc):
+        raise ValueError("cost / delegate cost buffer has the wrong size")
+    rc = lib().gs_delegate_cost(_dev(cost, torch.int32, "cost"), ctypes.byref(p.c()), int(b),
+                                _dev(coarse, torch.int32, "coarse"),
+                                _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_delegate_cost")
+
+
+def gs_skin_bounds(coarse_labels: torch.Tensor, p: Params, b: int, lo: torch.Tensor,
+                   hi: torch.Tensor, status: torch.Tensor, stream=None):
+    pc = gs_delegate_params(p, b)
+    if coarse_labels.numel() != pc.ng * pc.h or lo.numel() != p.ng * p.h or hi.numel() != p.ng * p.h:
+        raise ValueError("labels / bounds buffer has the wrong size")
+    rc = lib().gs_skin_bounds(_dev(coarse_labels, torch.int32, "coarse_labels"), ctypes.byref(p.c()),
+                              int(b), _dev(lo, torch.int32, "lo"), _dev(hi, torch.int32, "hi"),
+                              _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_skin_bounds")
+
+
+def gs_build_graph_skin(cost: torch.Tensor, p: Params, lo: torch.Tensor, hi: torch.Tensor,
+                        graph: torch.Tensor, status: torch.Tensor, stream=None):
+    if graph.numel() < gs_graph_bytes(p) or cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("graph / cost buffer has the wrong size")
+    if lo.numel() != p.ng * p.h or hi.numel() != p.ng * p.h:
+        raise ValueError("bounds must hold h * n_g entries")
+    rc = lib().gs_build_graph_skin(_dev(cost, torch.int32, "cost"), ctypes.byref(p.c()),
+                                   _dev(lo, torch.int32, "lo"), _dev(hi, torch.int32, "hi"),
+                                   _dev(graph, torch.uint8, "graph"),
+                                   _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_build_graph_skin")
+
+
 # ---------------------------------------------------------- whole pairs ---
 
 class Buffers:
@@ -345,6 +396,42 @@ def solve_costs(cost: torch.Tensor, p: Params, o: SolveOpts | None = None,
     gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status, stream)
     gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status, stream)
     return buf.labels, buf.flow, buf.status
+
+
+class Level1Buffers:
+    """Device buffers of the level-1 approximation for one size and block size."""
+
+    def __init__(self, p: Params, b: int, o: SolveOpts, oc: SolveOpts | None = None,
+                 device="cuda"):
+        self.p, self.b, self.o = p, b, o
+        self.pc = gs_delegate_params(p, b)
+        self.oc = oc or o
+        self.coarse = Buffers(self.pc, self.oc, device=device)
+        self.fine = Buffers(p, o, device=device)
+        self.lo = torch.empty((p.h, p.ng), dtype=torch.int32, device=device)
+        self.hi = torch.empty((p.h, p.ng), dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def solve_level1(cost: torch.Tensor, p: Params, b: int, o: SolveOpts | None = None,
+                 bufs: Level1Buffers | None = None, stream=None):
+    """Level-1 approximation of §4.5 from a cost volume int32 [h, n_g, D]:
+    delegate cut, thin skin, exact second cut.  Returns (labels, coarse_labels,
+    status) device tensors; status is the first non-OK status of the steps."""
+    o = o or SolveOpts()
+    bufs = bufs or Level1Buffers(p, b, o, device=cost.device)
+    c = cost.reshape(-1)
+    cb, fb = bufs.coarse, bufs.fine
+    gs_delegate_cost(c, p, b, cb.cost, bufs.status, stream)
+    gs_build_graph(cb.cost, bufs.pc, cb.graph, cb.status, stream)
+    gs_maxflow_solve(cb.graph, bufs.pc, bufs.oc, cb.work, cb.status, stream)
+    gs_extract_labels(cb.graph, bufs.pc, bufs.oc, cb.work, cb.labels, cb.flow, cb.status, stream)
+    gs_skin_bounds(cb.labels, p, b, bufs.lo, bufs.hi, bufs.status, stream)
+    gs_build_graph_skin(c, p, bufs.lo, bufs.hi, fb.graph, fb.status, stream)
+    gs_maxflow_solve(fb.graph, p, o, fb.work, fb.status, stream)
+    gs_extract_labels(fb.graph, p, o, fb.work, fb.labels, fb.flow, fb.status, stream)
+    st = torch.where(bufs.status != 0, bufs.status, torch.where(cb.status != 0, cb.status, fb.status))
+    return fb.labels, cb.labels, st
 
 
 # ------------------------------------------------------------- batches ---

@@ -86,3 +86,24 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
                 assert "gazecut_oracle" not in txt, f
+
+
+def test_delegate_params_on_host(lib):
+    """Delegate problem sizes and weights of the level-1 approximation (§4.5)
+    are computed on the host; bad block sizes are refused."""
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10, inhibit=1023)
+    q = gc.gs_delegate_params(p, 3)
+    assert (q.ng, q.h, q.D) == (118, 96, 6)
+    assert (q.lam, q.inhibit, q.vertical_inhibit) == (30, 3069, 1)
+    assert gc.gs_delegate_params(p, 1).c().w == p.c().w
+    out = gc.GsParams()
+    for b in (0, 16, -1):
+        assert lib.gs_delegate_params(ctypes.byref(p.c()), b, ctypes.byref(out)) == gc.GS_ERR_INVAL
+    big = gc.Params(w=64, h=4, D=8, tau=1, lam=1 << 27, inhibit=0)
+    assert lib.gs_delegate_params(ctypes.byref(big.c()), 4, ctypes.byref(out)) == gc.GS_ERR_OVERFLOW
+    pp = p.c()
+    assert lib.gs_delegate_cost(None, ctypes.byref(pp), 2, None, None, None) == gc.GS_ERR_INVAL
+    assert lib.gs_skin_bounds(None, ctypes.byref(pp), 2, None, None, None, None) == gc.GS_ERR_INVAL
+    assert lib.gs_build_graph_skin(None, ctypes.byref(pp), None, None, None, None,
+                                   None) == gc.GS_ERR_INVAL
