@@ -305,6 +305,55 @@ def _differentiated(gc, dev, args, stream):
             "workload": "384x288, 32 depth numbers, learned FP32 cost at scale 256"}
 
 
+def _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream, with_oracle):
+    """Level-1 approximation (§4.5) on the main workload's pairs, block sizes
+    2 and 3: device time per pair from the images (cost volume, delegate cut,
+    skin, second cut, labels), energy gap against the exact minimum, and one
+    pair checked against the oracle."""
+    import torch
+    from paper_1803_01516_gb300 import autotune
+    out = {"workload": "the main workload's pairs", "block_sizes": {}}
+    cost = torch.empty(gc.gs_cost_volume_bytes(p) // 4, dtype=torch.int32, device=dev)
+    E = torch.zeros(1, dtype=torch.int64, device=dev)
+    for b in (2, 3):
+        pc = gc.gs_delegate_params(p, b)
+        bufs = gc.Level1Buffers(p, b, autotune.tuned_opts(p), autotune.tuned_opts(pc), device=dev)
+        ms, gaps, rel = [], [], []
+        for rep_ in range(4):
+            for k in range(len(Ld)):
+                flush.fill_(k & 0xff)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                gc.gs_stereo_cost_volume(Ld[k], Rd[k], p, cost)
+                X, _, st = gc.solve_level1(cost, p, b, bufs.o, bufs)
+                c.record(stream)
+                c.synchronize()
+                if int(st.item()) != gc.GS_OK:
+                    raise RuntimeError(f"level-1 status {int(st.item())}")
+                if rep_ == 0:
+                    continue                      # warm-up round
+                ms.append(a.elapsed_time(c))
+                gc.gs_energy(cost, X, p, E)
+                gap = int(E.item()) - exact_flows[k]
+                gaps.append(gap)
+                rel.append(gap / exact_flows[k])
+        entry = {"ms_per_pair": float(np.mean(ms)), "energy_gap_mean": float(np.mean(gaps)),
+                 "energy_gap_rel_mean": float(np.mean(rel)), "min_gap": int(min(gaps))}
+        if with_oracle and b == 2:
+            import oracle
+            from oracle import level1 as l1
+            gc.gs_stereo_cost_volume(Ld[0], Rd[0], p, cost)
+            X, Xc, _ = gc.solve_level1(cost, p, b, bufs.o, bufs)
+            C = cost.cpu().numpy().reshape(p.h, p.ng, p.D)
+            ref = l1.level1(C, p.lam, p.inhibit, 1, b)
+            entry["parity_vs_oracle"] = {
+                "pairs_checked": 1,
+                "labels_equal": bool(np.array_equal(X.cpu().numpy(), ref["labels"])),
+                "coarse_labels_equal": bool(np.array_equal(Xc.cpu().numpy(), ref["coarse_labels"]))}
+        out["block_sizes"][str(b)] = entry
+    return out
+
+
 def run(args):
     import torch
 
@@ -451,6 +500,15 @@ def run(args):
             ok_lab &= bool(np.array_equal(buf.labels.cpu().numpy(), ref["labels"]))
         parity = {"pairs": len(refs), "flow_equal": ok_flow, "labels_equal": ok_lab}
 
+    level1 = None
+    if not args.no_batched and world == 1:
+        exact_flows = []
+        for k in range(len(Ld)):
+            step(k)
+            torch.cuda.synchronize(dev)
+            exact_flows.append(int(buf.flow.item()))
+        level1 = _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream,
+                         not args.no_cpu_baseline)
     batched = None if args.no_batched or world > 1 else _batched(gc, dev, args, stream, flush)
     diff = None if args.no_batched or world > 1 else _differentiated(gc, dev, args, stream)
 
@@ -477,6 +535,7 @@ def run(args):
         "parity_vs_oracle": parity,
         "batched": batched,
         "differentiated": diff,
+        "level1_approximation": level1,
         "clocks": clk,
         "gpu_launches": int(launches),
         "solver": {k: float(np.mean([s[k] for s in stats])) for k in

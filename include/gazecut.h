@@ -302,15 +302,15 @@ GS_API int gs_skin_bounds(const int32_t *coarse_labels, const gs_params *p, int3
  * Graph of the second cut: the chain graph of gs_build_graph for the problem
  * as given (p->direction is ignored; the label-reversed twin is never taken)
  * with every site's labels held in [lo, hi] (int32 [h][n_g] each, device,
- * 0 <= lo <= hi <= D-1).  X >= lo keeps n_1..n_lo on the source side: n_lo gets
- * extra source capacity one above everything that can leave that set (the
- * data arc at lo and the penalty and inhibit arcs into neighbours' nodes that
- * are not held to the source side), so no cut that cuts it can be minimal; X
- * <= hi holds n_hi+1.. on the sink side the same way with extra sink
- * capacity.  The flow value gs_extract_labels reports for this graph includes
- * these capacities; the energy of the labels (gs_energy) is the restricted
- * minimum.  status as gs_build_graph, plus GS_ERR_INVAL for bounds out of
- * order.
+ * 0 <= lo <= hi <= D-1).  X >= lo holds n_1..n_lo on the source side and
+ * X <= hi holds n_hi+1..n_(D-1) on the sink side; held nodes are contracted
+ * into the terminals (arcs from source-held into free nodes become source
+ * capacity of the free node, arcs from free into sink-held nodes sink
+ * capacity), so only the nodes of the skin carry flow.  Solve with
+ * GS_MODE_EXACT.  The flow value gs_extract_labels reports for this graph is
+ * that of the contracted graph; the energy of the labels (gs_energy) is the
+ * restricted minimum.  status as gs_build_graph, plus GS_ERR_INVAL for bounds
+ * out of order.
  */
 GS_API int gs_build_graph_skin(const int32_t *cost, const gs_params *p, const int32_t *lo,
                                const int32_t *hi, void *graph, int32_t *status, void *stream);

@@ -120,62 +120,120 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
     block_sum_u64(src, &s.hdr->src_total);
 }
 
-// Skin bounds of the level-1 second cut (§4.5), one thread per site.  The
-// set n_1..n_lo of a site with lo >= 1 is held on the source side by extra
-// source capacity at n_lo: one above the capacity of every arc that leaves the
-// set for a node not held there, i.e. the data arc at lo (C(lo)), the penalty
-// arcs v_k -> u_k with lo_u < k <= lo ((lo - lo_u)_+ of them) and the inhibit
-// arcs v_k -> u_(k-1) with lo_u + 1 < k <= lo ((lo - lo_u - 1)_+).  A cut that
-// left part of the set on the sink side would pay that extra arc; moving every
-// such set back to the source side saves it and adds less than it, so a
-// minimum cut keeps the bounds.  n_hi+1..n_(D-1) is held on the sink side by
-// extra sink capacity (a deficit) at n_hi+1, counted over the arcs that enter
-// the set the same way.  Totals join the header sums that the overflow check
-// and the flow value use.
-__global__ void k_skin(const int32_t *__restrict__ C, const int32_t *__restrict__ lo,
-                       const int32_t *__restrict__ hi, Geom g, State s, int32_t *status) {
-    unsigned long long src = 0, dfc = 0;
+// Graph of the level-1 second cut (§4.5), one thread per node.  With bounds
+// lo <= X <= hi a site's chain splits into nodes held on the source side
+// (k <= lo), free nodes (lo < k <= hi) and nodes held on the sink side
+// (k > hi).  Held nodes are contracted into the terminals: an arc from a
+// source-held node into a free node is a source arc (saturated at once: its
+// capacity is excess of the free node), an arc from a free node into a
+// sink-held node is a sink arc (its capacity is a deficit), and arcs among
+// held nodes are constants of the cut.  Residuals are set so that no
+// capacity leaves the source-held region and none enters the sink-held one:
+// source-held nodes can then never reach a deficit (their height stays
+// infinite), sink-held nodes never receive flow, and only the free nodes
+// carry the max-flow.  The free part of a chain is the chain of labels
+// lo..hi (source arc C(lo), sink arc C(hi)) with the same chain-local
+// preflow as k_build.  A source-held node keeps an excess of 1 so that label
+// extraction finds it on the source side.
+__device__ __forceinline__ int held(int lo, int hi, int k) { return k <= lo ? 0 : k > hi ? 2 : 1; }
+
+__global__ void k_build_skin(const int32_t *__restrict__ C, const int32_t *__restrict__ lo,
+                             const int32_t *__restrict__ hi, Geom g, State s, int32_t *status) {
+    unsigned long long src = 0, snk = 0;
     int bad = 0, big = 0;
-    const int64_t sites = (int64_t)g.ng * g.h;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < sites;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int W = (int)(v % g.ng), y = (int)(v / g.ng);
-        const int a = lo[v], b = hi[v];
-        if (a < 0 || a > b || b > g.D - 1) {
-            bad = 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const NodePos p = node_pos(g, i);
+        if (p.W >= g.ng) {
+            s.rc[i] = s.rr[i] = s.rd[i] = 0;
+            s.ri0[i] = s.ri1[i] = s.ri2[i] = s.ri3[i] = 0;
+            s.ex[i] = 0;
+            s.ht[i] = kInfH;
             continue;
         }
+        const int64_t v = (int64_t)p.y * g.ng + p.W;
+        auto lo_of = [&](int64_t u) {
+            const int a = lo[u], b = hi[u];
+            return (a < 0 || a > b || b > g.D - 1) ? 0 : a;
+        };
+        auto hi_of = [&](int64_t u) {
+            const int a = lo[u], b = hi[u];
+            return (a < 0 || a > b || b > g.D - 1) ? g.D - 1 : b;
+        };
+        bad |= lo[v] < 0 || lo[v] > hi[v] || hi[v] > g.D - 1;
+        const int a = lo_of(v), b = hi_of(v);
+        const int k = p.j + 1;
+        const int me = held(a, b, k);
         const int32_t *cs = C + v * g.D;
-        const int64_t nb[4] = {W > 0 ? v - 1 : -1, W + 1 < g.ng ? v + 1 : -1,
-                               y > 0 ? v - g.ng : -1, y + 1 < g.h ? v + g.ng : -1};
-        if (a >= 1) {
-            long long x = (long long)cs[a] + 1;
-            for (int q = 0; q < 4; q++) {
-                if (nb[q] < 0) continue;
-                const long long d = a - lo[nb[q]];
-                const long long h2 = q < 2 ? g.h2h : g.h2v;
-                x += (long long)g.lam * max(d, 0ll) + h2 * max(d - 1, 0ll);
-            }
-            big |= x > kCapLimit;
-            x = min(x, (long long)kCapLimit);
-            const int64_t i = ((int64_t)y * g.K + (a - 1)) * g.P + W;
-            s.ex[i] += (int32_t)x;
-            src += (unsigned long long)x;
+        // neighbours: W-1, W+1, y-1, y+1 (the inhibit directions ri0..ri3)
+        const bool has[4] = {p.W > 0, p.W < g.ng - 1, p.y > 0, p.y < g.h - 1};
+        const int64_t nb[4] = {v - 1, v + 1, v - g.ng, v + g.ng};
+        const int32_t h2[4] = {g.h2h, g.h2h, g.h2v, g.h2v};
+        int nlo[4], nhi[4];
+        for (int q = 0; q < 4; q++) {
+            nlo[q] = has[q] ? lo_of(nb[q]) : 0;
+            nhi[q] = has[q] ? hi_of(nb[q]) : g.D - 1;
         }
-        if (b <= g.D - 2) {
-            long long x = (long long)cs[b] + 1;
-            for (int q = 0; q < 4; q++) {
-                if (nb[q] < 0) continue;
-                const long long d = hi[nb[q]] - b;
-                const long long h2 = q < 2 ? g.h2h : g.h2v;
-                x += (long long)g.lam * max(d, 0ll) + h2 * max(d - 1, 0ll);
+        // data arc n_k -> n_(k+1) and the chain-local preflow of the free part
+        long long ex = 0;
+        int32_t rc = 0;
+        if (me == 1) {
+            int32_t F = cs[a];
+            for (int l = a + 1; l < k; l++) F = min(F, cs[l]);
+            if (k == a + 1) src += (unsigned long long)max(cs[a], 0);
+            if (k < b) {
+                const int32_t F1 = min(F, cs[k]);
+                ex = (long long)F - F1;
+                rc = cs[k] - F1;
+            } else {
+                ex = (long long)F - cs[b];
+                snk += (unsigned long long)max(cs[b], 0);
             }
-            big |= x > kCapLimit;
-            x = min(x, (long long)kCapLimit);
-            const int64_t i = ((int64_t)y * g.K + b) * g.P + W;
-            s.ex[i] -= (int32_t)x;
-            dfc += (unsigned long long)x;
+            for (int q = 0; q < 4; q++) {
+                if (!has[q]) continue;
+                const int hp = held(nlo[q], nhi[q], k);
+                if (hp == 0) { ex += g.lam; src += g.lam; }               // source-held -> me
+                if (hp == 2) { ex -= g.lam; snk += g.lam; }               // me -> sink-held
+                if (k + 1 <= g.D - 1 && held(nlo[q], nhi[q], k + 1) == 0) {
+                    ex += h2[q];                                          // inhibit into me
+                    src += h2[q];
+                }
+                if (k >= 2 && held(nlo[q], nhi[q], k - 1) == 2) {
+                    ex -= h2[q];                                          // inhibit out of me
+                    snk += h2[q];
+                }
+            }
+        } else if (me == 0) {
+            ex = 1;
         }
+        big |= ex > kCapLimit || ex < -(long long)kCapLimit;
+        for (int l = 0; l < g.D; l++) bad |= cs[l] < 0;
+        // penalty pairs stored at this node: right (rr) and down (rd); the value
+        // is the residual of this node -> neighbour, the reverse is 2 lambda - r
+        auto pair_res = [&](int su, int sv) -> int32_t {
+            if (su == 1 && sv == 1) return g.lam;
+            if ((su == 0 && sv != 0) || (su == 1 && sv == 2)) return 0;       // leaves S / enters T
+            if ((su == 1 && sv == 0) || (su == 2 && sv != 2)) return g.lam2;  // the reverse does
+            return g.lam;                                                     // both held alike
+        };
+        s.rc[i] = p.j < g.K - 1 ? rc : 0;
+        s.rr[i] = has[1] ? pair_res(me, held(nlo[1], nhi[1], k)) : 0;
+        s.rd[i] = has[3] ? pair_res(me, held(nlo[3], nhi[3], k)) : 0;
+        int32_t ri[4];
+        for (int q = 0; q < 4; q++) {
+            ri[q] = 0;
+            if (p.j == 0 || !has[q]) continue;
+            const int hh = held(nlo[q], nhi[q], k - 1);
+            // source-held tail into a free or sink-held head, free tail into a
+            // sink-held head: folded into the terminals, no residual
+            ri[q] = ((me == 0 && hh != 0) || (me == 1 && hh == 2)) ? 0 : h2[q];
+        }
+        s.ri0[i] = ri[0];
+        s.ri1[i] = ri[1];
+        s.ri2[i] = ri[2];
+        s.ri3[i] = ri[3];
+        s.ex[i] = (int32_t)max(min(ex, (long long)kCapLimit), -(long long)kCapLimit);
+        s.ht[i] = 0;
     }
     if (__syncthreads_or(bad)) {
         if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_INVAL);
@@ -183,8 +241,8 @@ __global__ void k_skin(const int32_t *__restrict__ C, const int32_t *__restrict_
     if (__syncthreads_or(big)) {
         if (threadIdx.x == 0) atomicCAS(status, GS_OK, GS_ERR_OVERFLOW);
     }
+    block_sum_u64(snk, &s.hdr->init_deficit);
     block_sum_u64(src, &s.hdr->src_total);
-    block_sum_u64(dfc, &s.hdr->init_deficit);
 }
 
 __global__ void k_check_totals(const GraphHeader *hdr, int32_t *status) {
@@ -316,10 +374,9 @@ int gs_build_graph_skin(const int32_t *cost, const gs_params *p, const int32_t *
     GS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
     k_header<<<1, 1, 0, st>>>(s.hdr, g, p->inhibit, p->vertical_inhibit);
     k_decide<<<1, 1, 0, st>>>(s.hdr, 1);
-    k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
-    k_skin<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(cost, lo, hi, g, s, status);
+    k_build_skin<<<grid_for(g.N), 256, 0, st>>>(cost, lo, hi, g, s, status);
     k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
-    count_launches(5);
+    count_launches(4);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
