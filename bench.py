@@ -354,6 +354,35 @@ def _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream, with_oracle):
     return out
 
 
+def _prepass(gc, dev, p, o, Ld, Rd, flush, stream):
+    """Max-flow time with and without the chain-local initial flow (the
+    build's stand-in for the paper's wave-front pre-pass), same pairs."""
+    import torch
+    buf = gc.Buffers(p, o, device=dev)
+    out = {}
+    for name, flags in (("with_chain_prepass", gc.GS_BUILD_CHAIN_PREFLOW), ("without", 0)):
+        ms, flows = [], []
+        for rep_ in range(3):
+            for k in range(len(Ld)):
+                gc.gs_stereo_cost_volume(Ld[k], Rd[k], p, buf.cost)
+                gc.gs_build_graph_flags(buf.cost, p, flags, buf.graph, buf.status)
+                flush.fill_(k & 0xff)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+                c.record(stream)
+                gc.gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status)
+                c.synchronize()
+                if int(buf.status.item()) != gc.GS_OK:
+                    raise RuntimeError("solve status")
+                if rep_:
+                    ms.append(a.elapsed_time(c))
+                    flows.append(int(buf.flow.item()))
+        out[name] = {"maxflow_ms": float(np.mean(ms)), "flows": flows[:len(Ld)]}
+    out["same_flows"] = out["with_chain_prepass"]["flows"] == out["without"]["flows"]
+    return out
+
+
 def run(args):
     import torch
 
@@ -500,7 +529,7 @@ def run(args):
             ok_lab &= bool(np.array_equal(buf.labels.cpu().numpy(), ref["labels"]))
         parity = {"pairs": len(refs), "flow_equal": ok_flow, "labels_equal": ok_lab}
 
-    level1 = None
+    level1 = prepass = None
     if not args.no_batched and world == 1:
         exact_flows = []
         for k in range(len(Ld)):
@@ -509,6 +538,7 @@ def run(args):
             exact_flows.append(int(buf.flow.item()))
         level1 = _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream,
                          not args.no_cpu_baseline)
+        prepass = _prepass(gc, dev, p, o, Ld, Rd, flush, stream)
     batched = None if args.no_batched or world > 1 else _batched(gc, dev, args, stream, flush)
     diff = None if args.no_batched or world > 1 else _differentiated(gc, dev, args, stream)
 
@@ -536,6 +566,7 @@ def run(args):
         "batched": batched,
         "differentiated": diff,
         "level1_approximation": level1,
+        "initial_flow_prepass": prepass,
         "clocks": clk,
         "gpu_launches": int(launches),
         "solver": {k: float(np.mean([s[k] for s in stats])) for k in

@@ -131,11 +131,26 @@ GS_API int gs_stereo_cost_volume(const uint8_t *L, const uint8_t *R, int32_t pit
  *   inhibit arcs u_k -> v_(k-1), k >= 2, carry inhibit.  The source arc C_v(0)
  *   and sink arc C_v(D-1) are folded into positive / negative node excess
  *   (§4.4); heights start at 0.
+ * Initial flow (the stand-in for the paper's undisclosed "wave front fetch"
+ * pre-pass, §4.4): every chain starts with its own largest flow already pushed
+ * down it, node n_k holding min C(0..k-1) - min C(0..k) and the data arcs
+ * carrying the prefix minima; the max-flow only routes what the interaction
+ * terms change.  The cut is the same with or without it (see
+ * gs_build_graph_flags).
  * cost: int32 [h][n_g][D], every entry >= 0.  graph: gs_graph_bytes() bytes,
  * written entirely.  status: device int32[1], set to GS_OK, GS_ERR_INVAL
  * (negative cost) or GS_ERR_OVERFLOW (sum of source capacities > 2^30 or a
  * cost > 2^30).
  */
+#define GS_BUILD_CHAIN_PREFLOW 1   /* chain-local initial flow (gs_build_graph's default) */
+
+/* gs_build_graph with explicit build flags (0 or GS_BUILD_CHAIN_PREFLOW).  With
+ * flags = 0 only the source arcs start saturated (n_1 holds C(0), the last node
+ * a deficit of C(D-1), every data arc unused): the textbook initial preflow,
+ * kept to measure what the pre-pass saves.  GS_ERR_INVAL for unknown flags. */
+GS_API int gs_build_graph_flags(const int32_t *cost, const gs_params *p, int32_t flags,
+                                void *graph, int32_t *status, void *stream);
+
 GS_API int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t *status,
                    void *stream);
 

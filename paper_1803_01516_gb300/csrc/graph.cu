@@ -62,8 +62,11 @@ __global__ void k_decide(GraphHeader *hdr, int direction) {
 //   rc = C(j+1) - F_(j+1)  residual of the outgoing data arc.
 // This is a valid preflow (the flow of every chain taken alone, i.e. the cut
 // with no interaction terms); the max-flow routes the rest.  Penalty residuals
-// start at lambda (no flow) and inhibit residuals at h2.
-__global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t *status) {
+// start at lambda (no flow) and inhibit residuals at h2.  Without the chain
+// pre-pass (preflow = 0) only the source arcs are saturated: n_1 holds C(0),
+// the last node's deficit is C(D-1), every data arc is unused.
+__global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t *status,
+                        int preflow) {
     unsigned long long deficit = 0, src = 0;
     int bad = 0, big = 0;
     const bool rev = *(volatile int32_t *)&s.hdr->rev != 0;
@@ -84,12 +87,13 @@ __global__ void k_build(const int32_t *__restrict__ C, Geom g, State s, int32_t 
         bad |= F < 0;
         big |= F > kCapLimit;
         for (int q = 1; q <= p.j; q++) F = min(F, c(q));
+        if (!preflow) F = p.j == 0 ? c(0) : 0;
         const int32_t cout = c(p.j + 1);  // outgoing arc capacity
         bad |= cout < 0;
         big |= cout > kCapLimit;
         int32_t e, rc;
         if (p.j < g.K - 1) {
-            const int32_t F1 = min(F, cout);
+            const int32_t F1 = preflow ? min(F, cout) : 0;
             e = F - F1;
             rc = cout - F1;
         } else {
@@ -347,8 +351,14 @@ extern "C" {
 
 int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t *status,
                    void *stream) {
+    return gs_build_graph_flags(cost, p, GS_BUILD_CHAIN_PREFLOW, graph, status, stream);
+}
+
+int gs_build_graph_flags(const int32_t *cost, const gs_params *p, int32_t flags, void *graph,
+                         int32_t *status, void *stream) {
     Geom g;
     if (make_geom(p, &g) != GS_OK || !cost || !graph || !status) return GS_ERR_INVAL;
+    if (flags & ~GS_BUILD_CHAIN_PREFLOW) return GS_ERR_INVAL;
     if (((uintptr_t)graph & 255) != 0) return GS_ERR_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     State s = state_view(graph, g);
@@ -356,7 +366,7 @@ int gs_build_graph(const int32_t *cost, const gs_params *p, void *graph, int32_t
     k_header<<<1, 1, 0, st>>>(s.hdr, g, p->inhibit, p->vertical_inhibit);
     k_dir_sums<<<grid_for((int64_t)g.ng * g.h), 256, 0, st>>>(cost, g, s.hdr);
     k_decide<<<1, 1, 0, st>>>(s.hdr, p->direction);
-    k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status);
+    k_build<<<grid_for(g.N), 256, 0, st>>>(cost, g, s, status, flags & GS_BUILD_CHAIN_PREFLOW);
     k_check_totals<<<1, 1, 0, st>>>(s.hdr, status);
     count_launches(5);
     GS_CUDA_TRY(cudaGetLastError());

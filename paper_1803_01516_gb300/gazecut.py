@@ -33,7 +33,9 @@ EXPORTS = [
     "gs_stereo_cost_volume_f32", "gs_energy_backward", "gs_cost_volume_f32_backward",
     "gs_cost_add_at_labels", "gs_batch_workspace_bytes", "gs_solve_batched",
     "gs_delegate_params", "gs_delegate_cost", "gs_skin_bounds", "gs_build_graph_skin",
+    "gs_build_graph_flags",
 ]
+GS_BUILD_CHAIN_PREFLOW = 1
 
 
 class GsParams(ctypes.Structure):
@@ -126,6 +128,7 @@ def lib():
             "gs_num_nodes": ([pp], I64),
             "gs_stereo_cost_volume": ([P, P, I32, pp, P, P], ctypes.c_int),
             "gs_build_graph": ([P, pp, P, P, P], ctypes.c_int),
+            "gs_build_graph_flags": ([P, pp, I32, P, P, P], ctypes.c_int),
             "gs_maxflow_solve": ([P, pp, po, P, P, P], ctypes.c_int),
             "gs_extract_labels": ([P, pp, po, P, P, P, P, P], ctypes.c_int),
             "gs_energy": ([P, P, pp, P, P], ctypes.c_int),
@@ -213,6 +216,16 @@ def gs_build_graph(cost: torch.Tensor, p: Params, graph: torch.Tensor, status: t
                               _dev(graph, torch.uint8, "graph"), _dev(status, torch.int32, "status"),
                               _stream(stream))
     _check(rc, "gs_build_graph")
+
+
+def gs_build_graph_flags(cost: torch.Tensor, p: Params, flags: int, graph: torch.Tensor,
+                         status: torch.Tensor, stream=None):
+    if graph.numel() < gs_graph_bytes(p) or cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("graph / cost buffer has the wrong size")
+    rc = lib().gs_build_graph_flags(_dev(cost, torch.int32, "cost"), ctypes.byref(p.c()),
+                                    int(flags), _dev(graph, torch.uint8, "graph"),
+                                    _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_build_graph_flags")
 
 
 def gs_maxflow_solve(graph: torch.Tensor, p: Params, o: SolveOpts, workspace: torch.Tensor,

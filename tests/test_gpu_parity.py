@@ -182,3 +182,25 @@ def test_overflow_and_negative_cost_flagged(gc):
     C[2, 3, 1] = -1
     gc.gs_build_graph(torch.from_numpy(C).cuda().reshape(-1), p, buf.graph, buf.status)
     assert int(buf.status.item()) == gc.GS_ERR_INVAL
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("which", ["tiny", "main"])
+def test_chain_prepass_changes_time_not_the_cut(gc, engine, which):
+    """The chain-local initial flow is only a head start: building without it
+    gives the same flow and canonical labels (and both equal the oracle's)."""
+    wl = synth.TINY if which == "tiny" else synth.MAIN
+    L, R, _ = synth.make_pair(wl, 3)
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+    p = _params(gc, wl)
+    o = gc.SolveOpts(engine=engine)
+    c = torch.from_numpy(C).cuda().reshape(-1)
+    for flags in (0, gc.GS_BUILD_CHAIN_PREFLOW):
+        buf = gc.Buffers(p, o)
+        gc.gs_build_graph_flags(c, p, flags, buf.graph, buf.status)
+        gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+        gc.gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status)
+        assert int(buf.status.item()) == gc.GS_OK
+        assert int(buf.flow.item()) == ref["flow"]
+        assert np.array_equal(buf.labels.cpu().numpy(), ref["labels"])
