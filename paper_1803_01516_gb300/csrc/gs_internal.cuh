@@ -86,7 +86,7 @@ static_assert(sizeof(Ctrl) <= 256, "ctrl block");
 // Control region at the start of a workspace: the Ctrl block (256 bytes),
 // then the control words of the persistent kernel's grid barrier and
 // per-step sums.
-constexpr size_t kWorkCtrlBytes = 8192;
+constexpr size_t kWorkCtrlBytes = 24576;
 
 struct Work {
     Ctrl *ctrl;

@@ -767,24 +767,24 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
 
 // ------------------------------------------------------- the solve loop ---
 //
-// One cooperative launch solves n independent pairs in steps separated by
-// grid barriers; in a step each pair's tiles with work do its current phase:
+// One cooperative launch solves n independent pairs.  Each pair runs its own
+// sequence of steps; in a step each of its tiles with work does the pair's
+// current phase:
 //
 //   INIT   first relabel pass (masks, heights reset, in-tile distances)
 //   PASS   later relabel pass (all tiles once, then tiles whose halo changed)
 //   SWEEP  one sweep round over the tiles with work
+//   LABELS label extraction (extraction launches)
 //   DONE   nothing
 //
-// A step's work items are the pairs' segments laid end to end: all T tiles of
-// a pair in INIT, its first PASS, its first SWEEP round (those with active
-// nodes) or LABELS; otherwise the tiles queued for this step by the visits of
-// the step before.  Blocks claim items one at a time from a counter, so a step
-// ends when the items run out, not when the block with the most tiles of a
-// fixed share finishes.
-//
-// After each barrier every block advances every pair's state machine from the
-// same per-pair sums (so all blocks take the same decisions) -- a pair that is
-// in its tail no longer leaves the grid idle when others still have work.
+// A step's work items are all T tiles of the pair (INIT, the first PASS, the
+// first SWEEP round -- those with active nodes -- and LABELS) or the tiles
+// queued for it by the visits of the step before.  Blocks claim items one at
+// a time from a per-pair claim word (step | items | next item), taking them
+// from any pair that has some; the block that completes a step's last item
+// advances that pair's state machine and publishes its next step.  There is
+// no grid barrier: a pair in a latency-bound tail steps as fast as its own
+// visits allow while other blocks work on other pairs.
 // Per pair the schedule is the one of a single solve: a relabel (capped at
 // relabel_passes passes unless it decides termination), then sweep rounds --
 // sweeps_per_relabel of them, or in the tail (few active nodes) until the
@@ -799,32 +799,50 @@ struct PairState {
     long long round, nrounds, rounds_total, relabels, passes, outer;
     long long active, prev1, prev2, relabel_visits, relabel_depth, last_relabel_depth, sweep_depth;
     long long visits_sweep_total, visits_relabel_total;
-    long long ns_sweep, ns_relabel;    // device time of the steps in each phase (block 0's clock)
+    long long ns_sweep, ns_relabel;    // device time of the steps in each phase
+    unsigned long long t_step;         // start of the current step (global timer)
 };
+
+// Per-pair control words of a launch.  claim packs the current step (16 bits,
+// for the queue slots), its number of items and the next item (24 bits each):
+// one atomic add both claims an item and tells which step it belongs to.
+struct PairCtl {
+    unsigned long long claim;
+    unsigned int done;      // items of the current step completed
+    unsigned int step;      // current step
+    long long red[3][4];    // per-step sums (slot = step mod 3)
+    int32_t qcount[3];      // queued tiles per step slot
+    int32_t pad;
+    PairState st;           // written only by the block that advances the pair
+};
+
+constexpr unsigned kItemMask = 0xffffffu;
+constexpr unsigned long long kIdleLimitNs = 60ull * 1000 * 1000 * 1000;   // an idle block gives up
+
+static_assert(sizeof(PairState) % 8 == 0, "PairState is copied in 8-byte words");
+
+// Copy of a pair's state as other SMs wrote it (L2-coherent loads).
+__device__ __forceinline__ void load_state(PairState *dst, const PairState *src) {
+    const long long *s = (const long long *)src;
+    long long *d = (long long *)dst;
+    for (int i = 0; i < (int)(sizeof(PairState) / 8); i++) d[i] = __ldcg(s + i);
+}
+
+__device__ __forceinline__ unsigned long long pack_claim(unsigned step, unsigned items,
+                                                         unsigned next) {
+    return ((unsigned long long)(step & 0xffffu) << 48) |
+           ((unsigned long long)(items & kItemMask) << 24) | (next & kItemMask);
+}
 
 struct BatchArgs {
     int n;            // pairs
-    int T_total;      // tiles over all pairs
     int extract;      // 0: max-flow solve, 1: label extraction
-    int tile_off[kMaxPairs + 1];
-    Ctrl *bar;        // grid barrier and abort flag
-    long long *red;   // per-step, per-pair sums [3][n][4]
-    int32_t *claim;   // per-step claim counters [3]
-    int32_t *qcount;  // per-step, per-pair lengths of the tile queues [3][kMaxPairs]
+    Ctrl *bar;        // abort flag and the count of finished pairs (Ctrl::active)
+    PairCtl *ctl;     // [n]
     SolveArgs pair[kMaxPairs];
 };
 
 static_assert(sizeof(BatchArgs) <= 32000, "the batch arguments travel as kernel parameters");
-
-__device__ __forceinline__ int pair_of(const BatchArgs &B, int gt) {
-    int lo = 0, hi = B.n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (B.tile_off[mid] <= gt) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 __device__ void start_relabel(PairState &st, const SolveArgs &a) {
     if (a.mode == GS_MODE_EXACT && st.outer >= a.max_iters) {
@@ -844,7 +862,7 @@ __device__ __forceinline__ long long step_depth(long long visits) {
     return max(1ll, (visits + gridDim.x - 1) / gridDim.x);
 }
 
-// Advance one pair after a barrier; v = this step's sums {a, b, c, overflow}.
+// Advance one pair at the end of a step; v = the step's sums {a, b, c, overflow}.
 __device__ void advance(PairState &st, const SolveArgs &a, const long long v[4], int extract) {
     if (v[3] && st.status == GS_OK) {
         st.status = GS_ERR_OVERFLOW;
@@ -969,78 +987,161 @@ __device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
     return block_sum((long long)deficit);
 }
 
-// Phases whose work items this step are the tiles queued by the step before.
+// Phases whose items are the tiles queued by the step before.
 __device__ __forceinline__ bool queued(const PairState &st) {
     return (st.phase == PH_PASS && st.pass > 1) || (st.phase == PH_SWEEP && st.round > 0);
 }
 
-// Claim this step's next work item (thread 0): the global tile index, or -1
-// when the items have run out.  A first sweep round skips tiles whose last
-// relabel pass left no active node.
-__device__ int claim_item(const BatchArgs &B, const PairState *S, const int *seg, int slot) {
-    const int V = seg[B.n];
-    for (;;) {
-        const int v = atomicAdd(&B.claim[slot], 1);
-        if (v >= V) return -1;
-        int lo = 0, hi = B.n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (seg[mid] <= v) lo = mid;
-            else hi = mid - 1;
-        }
-        const SolveArgs &a = B.pair[lo];
-        const int idx = v - seg[lo];
-        int tile = idx;
-        if (queued(S[lo])) tile = ld(&a.tile_list[slot * a.t.T + idx]);
-        else if (S[lo].phase == PH_SWEEP && ld(&a.tile_cnt[tile]) <= 0) continue;
-        return B.tile_off[lo] + tile;
+// Items of a pair's step from its state and the queue the step before filled.
+__device__ __forceinline__ unsigned step_items(const PairState &st, const SolveArgs &a,
+                                               const PairCtl *c, unsigned step) {
+    if (st.phase == PH_DONE) return 0;
+    return queued(st) ? (unsigned)*(volatile const int32_t *)&c->qcount[step % 3] : (unsigned)a.t.T;
+}
+
+// Statistics and results of a finished pair.
+__device__ void pair_results(const BatchArgs &B, const PairState &st, const SolveArgs &a,
+                             int status) {
+    if (!B.extract) {
+        Ctrl *c = a.ctrl;
+        c->stats[0] = st.relabels;
+        c->stats[1] = st.rounds_total;
+        c->stats[2] = st.passes;
+        c->stats[4] = st.active;
+        c->stats[5] = st.ns_sweep;
+        c->stats[6] = st.ns_relabel;
+        c->stats[7] = 1;
+        c->visits_sweep = st.visits_sweep_total;
+        c->visits_relabel = st.visits_relabel_total;
+        c->converged = st.phase == PH_DONE && status == GS_OK;
+    } else {
+        a.ctrl->stats[3] = st.passes;
+        *a.flow = (int64_t)a.s.hdr->init_deficit - st.active;
     }
+    if (status != GS_OK) atomicCAS(a.status, GS_OK, status);
+}
+
+// End of a pair's step (one thread, after every item completed): advance the
+// state machine -- through any steps that have no items -- and publish the
+// next step's claim word, or count the pair finished.
+__device__ void end_step(const BatchArgs &B, int p) {
+    PairCtl *c = B.ctl + p;
+    const SolveArgs &a = B.pair[p];
+    __threadfence();
+    PairState st;
+    load_state(&st, &c->st);
+    unsigned step = *(volatile unsigned *)&c->step;
+    unsigned items = 0;
+    const unsigned long long t_now = now_ns();
+    if (st.phase == PH_SWEEP) st.ns_sweep += (long long)(t_now - st.t_step);
+    else st.ns_relabel += (long long)(t_now - st.t_step);
+    st.t_step = t_now;
+    for (;;) {
+        long long v[4];
+        for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&c->red[step % 3][k];
+        advance(st, a, v, B.extract);
+        const unsigned next = step + 1;
+        for (int k = 0; k < 4; k++) c->red[next % 3][k] = 0;
+        c->qcount[(next + 1) % 3] = 0;
+        items = step_items(st, a, c, next);
+        step = next;
+        if (st.phase == PH_DONE || items > 0) break;
+    }
+    c->st = st;
+    c->done = 0;
+    c->step = step;
+    if (st.phase == PH_DONE) pair_results(B, st, a, st.status);
+    __threadfence();
+    atomicExch(&c->claim, pack_claim(step, items, 0));
+    if (st.phase == PH_DONE) atomicAdd(&B.bar->active, 1);
 }
 
 template <int NPT>
 __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant__ BatchArgs B) {
     extern __shared__ int32_t smem[];
-    __shared__ PairState S[kMaxPairs];
-    __shared__ int s_seg[kMaxPairs + 1];   // this step's work items: prefix offsets per pair
-    __shared__ int s_claim[2];
-    for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
-        PairState st;
-        memset(&st, 0, sizeof(st));
-        st.status = GS_OK;
-        st.cap = B.pair[p].relabel_passes;
-        start_relabel(st, B.pair[p]);
-        S[p] = st;
+    __shared__ int s_claim[4];     // pair, item, step (low 32 bits), exit flag
+    __shared__ PairState s_st;
+    // block 0 starts every pair and publishes its first step
+    if (blockIdx.x == 0) {
+        for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
+            PairCtl *c = B.ctl + p;
+            PairState st;
+            memset(&st, 0, sizeof(st));
+            st.status = GS_OK;
+            st.cap = B.pair[p].relabel_passes;
+            st.t_step = now_ns();
+            start_relabel(st, B.pair[p]);
+            c->st = st;
+            c->step = 0;
+            c->done = 0;
+            const unsigned items = step_items(st, B.pair[p], c, 0);
+            if (st.phase == PH_DONE) pair_results(B, st, B.pair[p], st.status);
+            __threadfence();
+            atomicExch(&c->claim, pack_claim(0, items, 0));
+            if (st.phase == PH_DONE) atomicAdd(&B.bar->active, 1);
+        }
     }
-    __syncthreads();
-    unsigned long long t_step = now_ns();
-    for (long long step = 0;; step++) {
-        const int slot = (int)(step % 3), next = (int)((step + 1) % 3);
-        long long *red = B.red + slot * B.n * 4;
-        // work items per pair, then their prefix offsets
-        for (int p = threadIdx.x; p < B.n; p += blockDim.x)
-            s_seg[p + 1] = queued(S[p]) ? *(volatile int32_t *)&B.qcount[slot * kMaxPairs + p]
-                                        : (S[p].phase == PH_DONE ? 0 : B.pair[p].t.T);
-        __syncthreads();
+    for (;;) {
+        // claim an item of any pair (thread 0); idle polling backs off to 256 ns
         if (threadIdx.x == 0) {
-            s_seg[0] = 0;
-            for (int p = 0; p < B.n; p++) s_seg[p + 1] += s_seg[p];
+            const unsigned long long t0 = now_ns();
+            int got = 0;
+            for (int spin = 0; !got; spin++) {
+                if (aborted(B.bar) || *(volatile int32_t *)&B.bar->active >= B.n) {
+                    s_claim[3] = 1;
+                    break;
+                }
+                for (int k = 0; k < B.n && !got; k++) {
+                    const int p = (int)((blockIdx.x + k) % B.n);
+                    PairCtl *c = B.ctl + p;
+                    const unsigned long long w0 = *(volatile unsigned long long *)&c->claim;
+                    if ((w0 & kItemMask) >= ((w0 >> 24) & kItemMask)) continue;
+                    const unsigned long long w = atomicAdd(&c->claim, 1ull);
+                    const unsigned items = (unsigned)((w >> 24) & kItemMask);
+                    const unsigned idx = (unsigned)(w & kItemMask);
+                    if (idx >= items) continue;
+                    __threadfence();
+                    s_claim[0] = p;
+                    s_claim[1] = (int)idx;
+                    s_claim[2] = (int)*(volatile unsigned *)&c->step;
+                    s_claim[3] = 0;
+                    load_state(&s_st, &c->st);
+                    got = 1;
+                }
+                if (!got) {
+                    if (now_ns() - t0 > kIdleLimitNs) {
+                        atomicExch(&B.bar->abort, 1);
+                        s_claim[3] = 1;
+                        break;
+                    }
+                    __nanosleep(32u << min(spin, 3));
+                }
+            }
         }
         __syncthreads();
-        for (int it = 0;; it++) {
-            if (threadIdx.x == 0) s_claim[it & 1] = claim_item(B, S, s_seg, slot);
-            __syncthreads();
-            const int gt = s_claim[it & 1];
-            if (gt < 0) break;
-            const int pr = pair_of(B, gt);
-            const int tile = gt - B.tile_off[pr];
-            const SolveArgs &a = B.pair[pr];
-            const int phase = S[pr].phase;
-            const TileSmem m = tile_smem(smem, a.t.PN);
-            const int T = a.t.T;
-            int32_t *list_next = a.tile_list + next * T;
-            int32_t *count_next = B.qcount + next * kMaxPairs + pr;
-            long long va = 0, vb = 0, vc = 0;
-            int ovf = 0;
+        if (s_claim[3]) break;
+        const int pr = s_claim[0];
+        const unsigned step = (unsigned)s_claim[2];
+        const int slot = (int)(step % 3), next = (int)((step + 1) % 3);
+        PairCtl *c = B.ctl + pr;
+        const SolveArgs &a = B.pair[pr];
+        const int phase = s_st.phase;
+        const int T = a.t.T;
+        const TileSmem m = tile_smem(smem, a.t.PN);
+        int32_t *list_next = a.tile_list + next * T;
+        int32_t *count_next = &c->qcount[next];
+        __shared__ int s_tile;
+        if (threadIdx.x == 0) {
+            int tile = s_claim[1];
+            if (queued(s_st)) tile = ld(&a.tile_list[slot * T + tile]);
+            else if (phase == PH_SWEEP && ld(&a.tile_cnt[tile]) <= 0) tile = -1;   // nothing to sweep
+            s_tile = tile;
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        long long va = 0, vb = 0, vc = 0;
+        int ovf = 0;
+        if (tile >= 0) {
             if (phase == PH_INIT) {
                 va = relabel_init_tile<NPT>(a, m, tile);
                 vc = 1;
@@ -1051,7 +1152,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                     __stcg(&a.tile_act[T + tile], 0);
                 }
             } else if (phase == PH_PASS) {
-                const int pass = S[pr].pass;
+                const int pass = s_st.pass;
                 int32_t *dcur = a.tile_dirty + (pass & 1) * T;
                 int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
                 if (pass > 1 && threadIdx.x == 0) __stcg(&dcur[tile], 0);
@@ -1060,9 +1161,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                 vb = ch;
                 vc = 1;
             } else if (phase == PH_SWEEP) {
-                const int cur = (int)(S[pr].round & 1);
+                const int cur = (int)(s_st.round & 1);
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
-                sweep_tile<NPT>(a, m, tile, cur, S[pr].tail ? a.tail_iters : a.local_iters, ovf,
+                sweep_tile<NPT>(a, m, tile, cur, s_st.tail ? a.tail_iters : a.local_iters, ovf,
                                 list_next, count_next);
                 ovf = __syncthreads_or(ovf);
                 va = 1;
@@ -1071,64 +1172,30 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                 va = labels_tile(a, tile, bad);
                 vb = bad;
             }
-            if (threadIdx.x == 0) {
-                long long *rp = red + pr * 4;
-                if (va) atomicAdd((unsigned long long *)&rp[0], (unsigned long long)va);
-                if (vb) atomicAdd((unsigned long long *)&rp[1], (unsigned long long)vb);
-                if (vc) atomicAdd((unsigned long long *)&rp[2], (unsigned long long)vc);
-                if (ovf) atomicAdd((unsigned long long *)&rp[3], 1ull);
-            }
         }
-        // the sums and the claim counter of step + 1 start from zero (their
-        // slots were last used two steps ago); so do the queues that step + 1
-        // fills for step + 2 (last read at the start of the step before this)
-        if (blockIdx.x == 0) {
-            for (int i = threadIdx.x; i < B.n * 4; i += blockDim.x)
-                B.red[next * B.n * 4 + i] = 0;
-            for (int i = threadIdx.x; i < B.n; i += blockDim.x)
-                B.qcount[((step + 2) % 3) * kMaxPairs + i] = 0;
-            if (threadIdx.x == 0) B.claim[next] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long *rp = c->red[slot];
+            if (va) atomicAdd((unsigned long long *)&rp[0], (unsigned long long)va);
+            if (vb) atomicAdd((unsigned long long *)&rp[1], (unsigned long long)vb);
+            if (vc) atomicAdd((unsigned long long *)&rp[2], (unsigned long long)vc);
+            if (ovf) atomicAdd((unsigned long long *)&rp[3], 1ull);
+            __threadfence();
+            // the step cannot end before this item does, so the claim word
+            // still holds this step's item count
+            const unsigned total = (unsigned)((*(volatile unsigned long long *)&c->claim >> 24) &
+                                              kItemMask);
+            if (atomicAdd(&c->done, 1u) + 1u == total) end_step(B, pr);
         }
-        grid_sync_sum(B.bar, 0);
-        if (aborted(B.bar)) break;
-        int done = 1;
-        const unsigned long long t_now = now_ns();
-        for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
-            long long v[4];
-            for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&red[p * 4 + k];
-            if (S[p].phase == PH_SWEEP) S[p].ns_sweep += (long long)(t_now - t_step);
-            else if (S[p].phase != PH_DONE) S[p].ns_relabel += (long long)(t_now - t_step);
-            advance(S[p], B.pair[p], v, B.extract);
-            done &= S[p].phase == PH_DONE;
-        }
-        t_step = t_now;
-        if (__syncthreads_and(done)) break;
+        __syncthreads();
     }
-    // per-pair results (block 0): statistics, flow value, status
-    if (blockIdx.x == 0) {
-        const bool ab = aborted(B.bar);
+    // pairs still running when the launch gave up
+    if (blockIdx.x == 0 && aborted(B.bar)) {
+        __syncthreads();
         for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
-            const SolveArgs &a = B.pair[p];
-            const PairState &st = S[p];
-            int status = st.status;
-            if (ab && status == GS_OK) status = GS_ERR_TIMEOUT;
-            if (!B.extract) {
-                Ctrl *c = a.ctrl;
-                c->stats[0] = st.relabels;
-                c->stats[1] = st.rounds_total;
-                c->stats[2] = st.passes;
-                c->stats[4] = st.active;
-                c->stats[5] = st.ns_sweep;
-                c->stats[6] = st.ns_relabel;
-                c->stats[7] = 1;
-                c->visits_sweep = st.visits_sweep_total;
-                c->visits_relabel = st.visits_relabel_total;
-                c->converged = st.phase == PH_DONE && status == GS_OK;
-            } else {
-                a.ctrl->stats[3] = st.passes;
-                *a.flow = (int64_t)a.s.hdr->init_deficit - st.active;
-            }
-            if (status != GS_OK) atomicCAS(a.status, GS_OK, status);
+            PairState st;
+            load_state(&st, &B.ctl[p].st);
+            if (st.phase != PH_DONE) pair_results(B, st, B.pair[p], GS_ERR_TIMEOUT);
         }
     }
 }
@@ -1196,6 +1263,8 @@ static int setup_args(const Geom &g, const State &s, const Work &w, const gs_sol
     a.g = g;
     a.s = s;
     if (!pick_tile(g, a.t, npt, smem, o->tile_w, o->tile_h)) return GS_ERR_INVAL;
+    // a step's item count travels in 24 bits of the claim word
+    if (a.t.T > (int)(kItemMask - 4096)) return GS_ERR_INVAL;
     char *extra = (char *)w.mark + round_up(g.N * sizeof(int32_t), 256);
     a.amask = (uint16_t *)extra;
     a.tile_act = (int32_t *)(extra + round_up(g.N * sizeof(uint16_t), 256));
@@ -1221,7 +1290,8 @@ static void solve_fields(SolveArgs &a, const gs_solve_opts *o) {
 // Cooperative launch of the batch kernel with the whole grid resident.  The
 // launch goes through cudaLaunchKernelEx with the cooperative attribute, so a
 // caller may capture it in a CUDA graph.
-static int launch_batch(const BatchArgs &B, int npt, size_t smem, cudaStream_t st) {
+static int launch_batch(const BatchArgs &B, int npt, size_t smem, int total_tiles,
+                        cudaStream_t st) {
     void (*kern)(const BatchArgs) = npt == 4 ? k_batch<4> : k_batch<8>;
     int dev = 0;
     GS_CUDA_TRY(cudaGetDevice(&dev));
@@ -1234,7 +1304,7 @@ static int launch_batch(const BatchArgs &B, int npt, size_t smem, cudaStream_t s
     GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem));
     if (per_sm < 1) return GS_ERR_INVAL;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(std::min(per_sm * sms, B.T_total));
+    cfg.gridDim = dim3(std::min(per_sm * sms, total_tiles));
     cfg.blockDim = dim3(kTileThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -1248,26 +1318,18 @@ static int launch_batch(const BatchArgs &B, int npt, size_t smem, cudaStream_t s
     return GS_OK;
 }
 
-// Control words of a batch launch: the barrier block, the per-step sums, the
-// claim counters and the queue lengths.
-constexpr size_t kBatchRedBytes = 3 * kMaxPairs * 4 * sizeof(long long);
-constexpr size_t kBatchCtrlBytes = 256 + kBatchRedBytes + 16 + 3 * kMaxPairs * sizeof(int32_t);
+// Control words of a batch launch: the abort flag and finished-pair count,
+// then one PairCtl per pair.
+constexpr size_t kBatchCtrlBytes = 256 + kMaxPairs * sizeof(PairCtl);
 static_assert(256 + kBatchCtrlBytes <= kWorkCtrlBytes, "a pair's workspace holds a batch's control");
 
 static int run_batch(BatchArgs &B, int npt, size_t smem, void *ctrl_mem, cudaStream_t st) {
     B.bar = (Ctrl *)ctrl_mem;
-    B.red = (long long *)((char *)ctrl_mem + 256);
-    B.claim = (int32_t *)((char *)ctrl_mem + 256 + kBatchRedBytes);
-    B.qcount = B.claim + 4;
+    B.ctl = (PairCtl *)((char *)ctrl_mem + 256);
     int total = 0;
-    for (int p = 0; p < B.n; p++) {
-        B.tile_off[p] = total;
-        total += B.pair[p].t.T;
-    }
-    B.tile_off[B.n] = total;
-    B.T_total = total;
-    GS_CUDA_TRY(cudaMemsetAsync(ctrl_mem, 0, kBatchCtrlBytes, st));
-    return launch_batch(B, npt, smem, st);
+    for (int p = 0; p < B.n; p++) total += B.pair[p].t.T;
+    GS_CUDA_TRY(cudaMemsetAsync(ctrl_mem, 0, 256 + (size_t)B.n * sizeof(PairCtl), st));
+    return launch_batch(B, npt, smem, total, st);
 }
 
 size_t batch_ctrl_bytes() { return kBatchCtrlBytes; }
