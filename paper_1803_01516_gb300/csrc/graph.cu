@@ -33,6 +33,7 @@ __global__ void k_header(GraphHeader *hdr, Geom g, int inhibit, int vinhibit) {
     hdr->init_deficit = 0;
     hdr->src_total = 0;
     hdr->sum_last = 0;
+    hdr->exact_heights = 0;
 }
 
 // Source capacity of each direction: sum of C(0) and of C(D-1).

@@ -47,6 +47,7 @@ struct GraphHeader {
     unsigned long long init_deficit;  // total sink capacity left after folding
     unsigned long long src_total;     // total source capacity
     unsigned long long sum_last;      // sum of C(D-1) over sites
+    int32_t exact_heights;            // 1: ht holds the exact distances of a finished solve
 };
 
 // Solver state: structure of arrays, each N int32, 256-byte aligned.

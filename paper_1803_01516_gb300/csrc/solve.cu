@@ -173,6 +173,8 @@ extern "C" int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_
     State s = state_view(graph, g);
     Work w = work_view(workspace, g);
     if (o->engine == GS_ENGINE_TILED) return tiled_solve(g, s, w, o, status, st);
+    // this engine leaves no exact-height mark for the extraction to reuse
+    GS_CUDA_TRY(cudaMemsetAsync(&s.hdr->exact_heights, 0, sizeof(int32_t), st));
     const int grid = grid_for(g.N);
     GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
     PhaseTimer t_sweep, t_relabel;

@@ -796,6 +796,8 @@ enum { PH_INIT = 0, PH_PASS = 1, PH_SWEEP = 2, PH_LABELS = 3, PH_DONE = 4 };
 
 struct PairState {
     int phase, pass, full, conv, tail, status, cap;
+    int exact_end;     // ended on a relabel run to its fixed point that found nothing active
+    int ht_labels;     // extraction reads the solve's exact heights (no relabel of its own)
     long long round, nrounds, rounds_total, relabels, passes, outer;
     long long active, prev1, prev2, relabel_visits, relabel_depth, last_relabel_depth, sweep_depth;
     long long visits_sweep_total, visits_relabel_total;
@@ -907,6 +909,7 @@ __device__ void advance(PairState &st, const SolveArgs &a, const long long v[4],
             if (st.active == 0) {
                 if (st.conv) {
                     st.phase = PH_DONE;
+                    st.exact_end = 1;
                 } else {
                     st.full = 1;     // nothing active within reach: decide with an exact relabel
                     start_relabel(st, a);
@@ -958,7 +961,7 @@ __device__ void advance(PairState &st, const SolveArgs &a, const long long v[4],
 }
 
 // Labels of one tile's sites and the tile's remaining sink capacity.
-__device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
+__device__ long long labels_tile(const SolveArgs &a, int tile, const int32_t *hsrc, int &bad) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const TileOrigin o = tile_origin(t, tile);
@@ -973,7 +976,7 @@ __device__ long long labels_tile(const SolveArgs &a, int tile, int &bad) {
         int64_t i = (int64_t)y * g.SY + W;
         int lab = 0, prev = 1;
         for (int j = 0; j < g.K; j++, i += g.P) {
-            const int32_t h = ld(&a.hgt[i]);
+            const int32_t h = ld(&hsrc[i]);
             const int in = dir == 1 ? (h < kInfH) : (h >= kInfH);
             b |= in && !prev;
             lab += in;
@@ -1014,6 +1017,9 @@ __device__ void pair_results(const BatchArgs &B, const PairState &st, const Solv
         c->visits_sweep = st.visits_sweep_total;
         c->visits_relabel = st.visits_relabel_total;
         c->converged = st.phase == PH_DONE && status == GS_OK;
+        // the heights are then the exact distances to the remaining sink
+        // capacity: an extraction that needs just those reuses them
+        if (st.exact_end && status == GS_OK) a.s.hdr->exact_heights = 1;
     } else {
         a.ctrl->stats[3] = st.passes;
         *a.flow = (int64_t)a.s.hdr->init_deficit - st.active;
@@ -1070,7 +1076,18 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
             st.status = GS_OK;
             st.cap = B.pair[p].relabel_passes;
             st.t_step = now_ns();
-            start_relabel(st, B.pair[p]);
+            const SolveArgs &a = B.pair[p];
+            if (!B.extract) {
+                a.s.hdr->exact_heights = 0;
+                start_relabel(st, a);
+            } else if (a.dir == 2 && ld(&a.s.hdr->rev) && ld(&a.s.hdr->exact_heights)) {
+                // the label-reversed problem's labels come from distances to the
+                // sink capacity, which the finished solve left exact in ht
+                st.phase = PH_LABELS;
+                st.ht_labels = 1;
+            } else {
+                start_relabel(st, a);
+            }
             c->st = st;
             c->step = 0;
             c->done = 0;
@@ -1169,7 +1186,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                 va = 1;
             } else {   // PH_LABELS
                 int bad = 0;
-                va = labels_tile(a, tile, bad);
+                va = labels_tile(a, tile, s_st.ht_labels ? a.s.ht : a.hgt, bad);
                 vb = bad;
             }
         }
