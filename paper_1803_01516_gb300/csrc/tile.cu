@@ -356,11 +356,7 @@ __device__ __forceinline__ int eff_dir(const SolveArgs &a) {
 // ---------------------------------------------------------- relabel pass ---
 
 // Local relaxation to the tile's fixed point.  Own nodes' residual-arc masks
-// are in registers (mk), own heights and halo heights in shared memory.  A
-// row of the tile (one depth layer of one site row) is revisited only while a
-// row it has arcs into (same, next and previous layer and site row) changed in
-// the previous iteration; three rotating bitmaps carry the changed rows.
-constexpr int kMaxRows = 1024;
+// are in registers (mk), own heights and halo heights in shared memory.
 
 template <int NPT>
 __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi)[NPT],
@@ -525,7 +521,6 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
                                        int32_t *count_next) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
-    const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
     load_halo(a, m, o, false, a.hgt);
     int pi[NPT];

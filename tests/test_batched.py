@@ -104,3 +104,43 @@ def test_batched_call_captured_in_a_cuda_graph(gc):
         assert int(b.status.item()) == gc.GS_OK
         assert int(b.flow.item()) == ref["flow"]
         assert np.array_equal(b.labels.cpu().numpy(), ref["labels"])
+
+
+def test_full_batch_with_trivial_and_timed_out_pairs(gc):
+    """64 pairs stepping independently: uneven random pairs, pairs with zero
+    cost (nothing to route, E* = 0) and one pair held to a single relabel
+    (GS_ERR_TIMEOUT) -- every other pair still ends exact and bit-equal to
+    the oracle, and the timed-out pair's state resumes to the exact cut."""
+    pairs = _uneven_batch(60, 7)
+    flat = np.full((12, 40), 77, np.uint8)
+    for i in range(3):
+        wl = synth.Workload(f"flat{i}", 40, 12, 6 + i, tau=30, lam=3, sigma=0.0, scene="layers",
+                            n_layers=1, n_slanted=0, max_disp=2, seed_base=1)
+        pairs.append((wl, flat, flat, 1))
+    tiny = synth.TINY
+    L, R, _ = synth.make_pair(tiny, 2)
+    pairs.append((tiny, L, R, 1))
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                        vertical_inhibit=vi) for wl, _, _, vi in pairs]
+    opts = [gc.SolveOpts() for _ in pairs]
+    opts[-1] = gc.SolveOpts(max_iters=1, sweeps_per_relabel=1)
+    batch = gc.Batch(params, opts)
+    Ls = [torch.from_numpy(np.ascontiguousarray(L)).cuda() for _, L, _, _ in pairs]
+    Rs = [torch.from_numpy(np.ascontiguousarray(R)).cuda() for _, _, R, _ in pairs]
+    gc.gs_solve_batched(batch, Ls, Rs)
+    torch.cuda.synchronize()
+    for i, ((wl, L, R, vi), p, b) in enumerate(zip(pairs, params, batch.bufs)):
+        C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+        ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
+        if i == len(pairs) - 1:
+            assert int(b.status.item()) == gc.GS_ERR_TIMEOUT
+            b.status.zero_()
+            o = gc.SolveOpts()
+            gc.gs_maxflow_solve(b.graph, p, o, b.work, b.status)
+            gc.gs_extract_labels(b.graph, p, o, b.work, b.labels, b.flow, b.status)
+            torch.cuda.synchronize()
+        assert int(b.status.item()) == gc.GS_OK, i
+        assert int(b.flow.item()) == ref["flow"], i
+        assert np.array_equal(b.labels.cpu().numpy(), ref["labels"]), i
+        if i >= 60 and i < 63:
+            assert ref["flow"] == 0
