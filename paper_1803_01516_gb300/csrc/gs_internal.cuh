@@ -70,11 +70,7 @@ struct Ctrl {
     int32_t changed;
     int32_t active;
     int32_t abort;
-    unsigned int bar_count;
-    unsigned int bar_gen;
     int32_t converged;
-    int32_t pad;
-    long long bar_red[2][2];
     long long stats[8];   // relabels, sweeps, bfs passes, label passes, active at exit,
                           // sweep ns, relabel ns, launches
     unsigned long long deficit_left;
@@ -85,8 +81,9 @@ struct Ctrl {
 static_assert(sizeof(Ctrl) <= 256, "ctrl block");
 
 // Control region at the start of a workspace: the Ctrl block (256 bytes),
-// then the control words of the persistent kernel's grid barrier and
-// per-step sums.
+// then the persistent kernel's control words (an abort flag and a finished-
+// pair count in a second Ctrl, then per pair its claim word, step, per-step
+// sums and queue lengths, and state machine).
 constexpr size_t kWorkCtrlBytes = 24576;
 
 struct Work {

@@ -5,8 +5,8 @@
 // tiles of TW sites x TH rows x all K chain layers (whole chains, so the data
 // arcs and their infinite reverse arcs never leave a tile).  A CTA stages a
 // tile plus a one-site halo in shared memory and works on it locally; tiles
-// exchange flow only through atomics on global memory, and CTAs meet at grid
-// barriers between phases:
+// exchange flow only through atomics on global memory, and a pair's steps
+// (see "the solve loop" below) separate its phases:
 //
 //   global relabel  heights = breadth-first distance to the nearest node with
 //                   sink capacity left, computed as a monotone relaxation:
@@ -33,7 +33,6 @@ namespace gs {
 
 constexpr int kTileThreads = 512;
 constexpr int kMaxTileNodes = 4096;           // own nodes per tile (8 per thread at most)
-constexpr long long kSpinLimit = 1ll << 24;   // grid-barrier wait bound (~1-2 s)
 
 struct TileGeom {
     int TW, TH;        // sites per tile along W and y
@@ -66,54 +65,6 @@ struct SolveArgs {
     int mode, sweeps_per_relabel, local_iters, relabel_passes, tail_iters;
     long long fixed_sweeps, max_iters;
 };
-
-// ------------------------------------------------------------ grid sync ---
-
-// Grid-wide barrier that also sums two values over the blocks (thread 0's
-// arguments count).  Waits are bounded: after kSpinLimit polls the block sets
-// ctrl->abort and leaves.
-struct Sum2 {
-    long long a, b;
-};
-
-__device__ Sum2 grid_sync_sum2(Ctrl *ctrl, long long va, long long vb) {
-    __shared__ long long s_res[2];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &ctrl->bar_gen;
-        const unsigned int gen = *vgen;
-        const int slot = gen & 1;
-        if (va) atomicAdd((unsigned long long *)&ctrl->bar_red[slot][0], (unsigned long long)va);
-        if (vb) atomicAdd((unsigned long long *)&ctrl->bar_red[slot][1], (unsigned long long)vb);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&ctrl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            ctrl->bar_count = 0;
-            ctrl->bar_red[slot ^ 1][0] = 0;
-            ctrl->bar_red[slot ^ 1][1] = 0;
-            __threadfence();
-            atomicAdd(&ctrl->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > kSpinLimit) {
-                    atomicExch(&ctrl->abort, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_res[0] = *(volatile long long *)&ctrl->bar_red[slot][0];
-        s_res[1] = *(volatile long long *)&ctrl->bar_red[slot][1];
-    }
-    __syncthreads();
-    return Sum2{s_res[0], s_res[1]};
-}
-
-__device__ __forceinline__ long long grid_sync_sum(Ctrl *ctrl, long long v) {
-    return grid_sync_sum2(ctrl, v, 0).a;
-}
 
 // Every read of solver state inside the persistent kernel bypasses L1: other
 // SMs update the same words during the launch, and L1 is not coherent.
