@@ -152,8 +152,15 @@ def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpt
     best = entry["best"]
     spr, li, rp = best[:3]
     tw, th = (best[3], best[4]) if len(best) == 5 else (0, 0)
-    return gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
-                        tile_h=th, **kw)
+    o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
+                     tile_h=th, **kw)
+    try:
+        gc.gs_tile_info(p, o)
+    except RuntimeError:
+        # a shape borrowed from another bucket may not fit this depth range:
+        # let the library choose one
+        o.tile_w = o.tile_h = 0
+    return o
 
 
 if __name__ == "__main__":

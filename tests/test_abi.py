@@ -107,3 +107,14 @@ def test_delegate_params_on_host(lib):
     assert lib.gs_skin_bounds(None, ctypes.byref(pp), 2, None, None, None, None) == gc.GS_ERR_INVAL
     assert lib.gs_build_graph_skin(None, ctypes.byref(pp), None, None, None, None,
                                    None) == gc.GS_ERR_INVAL
+
+
+def test_tuned_options_always_fit(lib):
+    """Options from the autotuner's table (or the nearest bucket's) give a
+    tile shape that fits the params, including depth ranges no bucket covers."""
+    from paper_1803_01516_gb300 import autotune
+    from paper_1803_01516_gb300 import gazecut as gc
+    for w, h, D in [(384, 288, 16), (1920, 1080, 128), (640, 480, 96), (200, 100, 4)]:
+        p = gc.Params(w=w, h=h, D=D, tau=30, lam=10)
+        o = autotune.tuned_opts(p)
+        gc.gs_tile_info(p, o)          # raises if the shape does not fit
