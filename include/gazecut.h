@@ -83,7 +83,8 @@ typedef struct gs_params {
 /* Solver engines.  Both compute the same exact cut; they differ in schedule.
  *   TILED   one persistent cooperative launch: shared-memory tiles of whole
  *           depth chains, local push/relabel iterations, tile-local relabel
- *           passes, grid barriers, no host synchronisation (default)
+ *           passes, tiles claimed per step from device-side queues, no host
+ *           synchronisation (default)
  *   SIMPLE  one thread per node, one kernel per sweep / relabel pass, host loop
  *           (a second, independent schedule kept for cross-checking) */
 #define GS_ENGINE_TILED  0
