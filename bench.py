@@ -29,6 +29,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -147,6 +148,59 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _cpu_info() -> dict:
+    """Host CPU model (first model line of /proc/cpuinfo) and core count."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "hardware", "cpu part", "processor name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def _oracle_pair_ms(item):
+    """One whole pair through the CPU oracle (a pool worker; no GPU)."""
+    D, dis0, tau, lam, inhibit, L, R = item
+    import oracle
+    t0 = time.perf_counter()
+    C = oracle.cost_volume(L, R, D, dis0, tau)
+    oracle.solve(C, lam, inhibit, 1, "bk")
+    return 1e3 * (time.perf_counter() - t0)
+
+
+def _batched_cpu_baseline(batch, n_sample=2):
+    """The oracle on the batch's n_sample pairs nearest its lower-quartile node
+    count (a pair near the median takes the oracle most of a minute), one pair
+    per process on the host cores (a spawn pool: no process forked from one
+    that holds a GPU context).  pairs/s = cores / mean time per pair, i.e. the
+    whole batch spread over all cores; the sample leaves out the batch's larger
+    pairs, on which Boykov-Kolmogorov is slower, so this rate favours the CPU."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    nodes = np.array([(wl.w - 2 * (wl.D - 1)) * wl.h * (wl.D - 1) for wl, _, _, _ in batch])
+    target = np.percentile(nodes, 25)
+    pick = [int(k) for k in np.argsort(np.abs(nodes - target))[:n_sample]]
+    items = [(batch[k][0].D, 2 * (batch[k][0].D - 1), batch[k][0].tau, batch[k][0].lam,
+              batch[k][0].inhibit, batch[k][1], batch[k][2]) for k in pick]
+    cores = os.cpu_count() or 1
+    workers = min(cores, n_sample)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        ms = pool.map(_oracle_pair_ms, items)
+    return {"value": 1e3 * cores / float(np.mean(ms)), "unit": "pairs/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"the {n_sample} of the {len(batch)} pairs nearest the lower-quartile node "
+                      f"count ({int(target)}; median {int(np.median(nodes))}), single-threaded "
+                      f"Boykov-Kolmogorov + cost volume "
+                      f"each, {workers} at a time; pairs/s = cores / mean time per pair "
+                      f"({float(np.mean(ms)):.0f} ms)", **_cpu_info()}
+
+
 def _cpu_baseline(wl, pairs):
     """The CPU oracle (cost volume + Boykov-Kolmogorov, single-threaded) on the
     bench's distinct pairs; returns the timing line and the oracle solutions."""
@@ -160,7 +214,8 @@ def _cpu_baseline(wl, pairs):
         times.append(time.perf_counter() - t0)
     cpu = {"value": 1e3 * float(np.mean(times)), "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"the {len(pairs)} distinct {wl.w}x{wl.h}x{wl.D} pairs of the timed steps, "
-                     "whole pairs, single-threaded Boykov-Kolmogorov + cost volume, mean ms/pair"}
+                     "whole pairs, single-threaded Boykov-Kolmogorov + cost volume, mean ms/pair",
+           **_cpu_info()}
     return cpu, refs
 
 
@@ -265,6 +320,8 @@ def _batched(gc, dev, args, stream, flush):
            "single_call_pairs_per_s": 1e3 * len(params) / t_single,
            "flows_match_single_calls": bool(ok),
            "workload": "64 pairs, w~U[160,640], h~U[120,480], D~U[16,64], layered scenes"}
+    if args.batched_cpu_baseline:
+        out["cpu_baseline"] = _batched_cpu_baseline(batch)
     if not args.no_cpu_baseline:
         import oracle
         order = np.argsort([gc.gs_num_nodes(p) for p in params])[:2]
@@ -594,6 +651,8 @@ def main():
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--diff-pairs", type=int, default=16)
+    ap.add_argument("--batched-cpu-baseline", action="store_true",
+                    help="also time the CPU oracle on batch pairs (about a minute)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
