@@ -160,6 +160,9 @@ def _cpu_info() -> dict:
                     break
     except OSError:
         pass
+    # Arm hosts list a part number instead of a name
+    model = {"0xd4f": "Arm Neoverse V2 (part 0xd4f)", "0xd40": "Arm Neoverse V1 (part 0xd40)",
+             "0xd0c": "Arm Neoverse N1 (part 0xd0c)"}.get(model.lower(), model)
     return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
