@@ -311,7 +311,7 @@ __device__ __forceinline__ int eff_dir(const SolveArgs &a) {
 
 template <int NPT>
 __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi)[NPT],
-                           const unsigned (&mk)[NPT]) {
+                           const unsigned (&mk)[NPT], int first_inner = 4) {
     const TileGeom &t = a.t;
     int off[kSlots];
 #pragma unroll
@@ -326,7 +326,10 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
     bool any_change = false;
     for (int outer = 0;; outer++) {
         int changed = 0;
-        for (int inner = 0; inner < kInner; inner++) {
+        // a first round of fewer sweeps settles tiles whose halo change does
+        // not reach them without paying for a full round
+        const int n_inner = outer == 0 ? first_inner : kInner;
+        for (int inner = 0; inner < n_inner; inner++) {
 #pragma unroll
             for (int k = 0; k < NPT; k++) {
                 if (pi[k] < 0) continue;
@@ -503,7 +506,8 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
     __shared__ int s_sides;
     if (threadIdx.x == 0) s_sides = 0;
     __syncthreads();
-    const bool ch = relax_tile<NPT>(a, m, pi, mk);
+    // one sweep first: most tiles a halo change marks need no more
+    const bool ch = relax_tile<NPT>(a, m, pi, mk, 1);
     int act = 0;
     unsigned sides = 0;
 #pragma unroll
