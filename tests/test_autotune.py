@@ -1,0 +1,53 @@
+"""Autotuner bookkeeping on the host: size buckets, cache before shipped
+defaults, nearest-bucket fallback and shapes that always fit (no GPU: tile
+shapes are checked with the library's host-side query)."""
+import json
+
+import pytest
+
+
+@pytest.fixture()
+def tune(monkeypatch, tmp_path):
+    from paper_1803_01516_gb300 import build
+    build.build()
+    from paper_1803_01516_gb300 import autotune
+    monkeypatch.setenv("GAZECUT_TUNE_CACHE", str(tmp_path / "cache.json"))
+    return autotune
+
+
+def test_buckets(tune):
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
+    assert tune.bucket(p) == "D16-n21"          # 354*288*15 = 1.53 M nodes
+    assert tune.bucket(gc.Params(w=640, h=480, D=64, tau=30, lam=10)) == "D64-n24"
+    assert tune.bucket(gc.Params(w=100, h=50, D=13, tau=30, lam=10)).startswith("D16-")
+
+
+def test_cache_overrides_shipped_defaults(tune):
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
+    shipped = tune.tuned_opts(p)
+    assert (shipped.tile_w, shipped.tile_h) != (0, 0)
+    with open(tune.cache_path(), "w") as f:
+        json.dump({tune.bucket(p): {"best": [8, 16, 4, 8, 8], "ms": 1.0}}, f)
+    o = tune.tuned_opts(p)
+    assert (o.sweeps_per_relabel, o.local_iters, o.relabel_passes, o.tile_w, o.tile_h) == \
+        (8, 16, 4, 8, 8)
+
+
+def test_nearest_bucket_and_fit(tune):
+    from paper_1803_01516_gb300 import gazecut as gc
+    # no entry for 128 depth numbers: the nearest bucket's schedule, a shape
+    # that fits (the borrowed one is too large for 127 layers)
+    p = gc.Params(w=1920, h=1080, D=128, tau=30, lam=10)
+    o = tune.tuned_opts(p)
+    info = gc.gs_tile_info(p, o)
+    assert info["smem_bytes"] <= 180 * 1024
+    assert o.sweeps_per_relabel >= 1 and o.local_iters >= 1
+
+
+def test_unparseable_keys_are_ignored(tune):
+    from paper_1803_01516_gb300 import gazecut as gc
+    table = {"junk": {"best": [1, 1, 1]}, "D16-n20": {"best": [32, 4, 8, 16, 8]}}
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
+    assert tune._nearest(table, p)["best"] == [32, 4, 8, 16, 8]
