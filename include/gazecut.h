@@ -232,7 +232,8 @@ GS_API int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params
               void *stream);
 
 /* Diagnostics of the last solve on this workspace: host int64[10] =
- * {global relabels, sweep rounds, relabel passes, label-extraction passes,
+ * {global relabels, sweep rounds, relabel passes, label-extraction passes (0
+ *  when the extraction read the finished solve's exact distances),
  *  active nodes at exit, device time of the sweep rounds in ns, device time
  *  of the global relabels in ns, kernel launches of the solve, tile visits of
  *  the sweep rounds, tile visits of the relabel passes}.  The times come from
