@@ -575,6 +575,16 @@ def run(args):
         * nodes_per_tile
     solve_s = float(np.mean(solve_ms)) * 1e-3
     achieved = alg_bytes / solve_s / 1e9
+    # per phase, over the device time the solver spent in each (its own clock)
+    sweep_ns = float(np.mean([s["sweep_ns"] for s in stats]))
+    relabel_ns = float(np.mean([s["relabel_ns"] for s in stats]))
+    per_phase = {
+        "sweep_rounds": {"achieved": BYTES_PER_NODE_SWEEP * sweep_visits * nodes_per_tile
+                         / max(sweep_ns, 1.0), "ms": sweep_ns * 1e-6},
+        "relabel_passes": {"achieved": BYTES_PER_NODE_BFS * relabel_visits * nodes_per_tile
+                           / max(relabel_ns, 1.0), "ms": relabel_ns * 1e-6}}
+    for v in per_phase.values():
+        v["frac"] = v["achieved"] / peak
 
     # ----- CPU oracle on the same pairs: baseline time and parity of the timed pairs -----
     cpu = None
@@ -617,7 +627,8 @@ def run(args):
                      "peak_kind": f"{peak_kind} HBM copy",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": solve_s * 1e3,
                      "accounting": "72 B/node per tile visit of a sweep round + 40 B/node per "
-                                   "tile visit of a relabel pass"},
+                                   "tile visit of a relabel pass",
+                     "per_phase": per_phase},
         "phases_ms": {"cost_volume+build": float(np.mean(build_ms)),
                       "maxflow_solve": float(np.mean(solve_ms)),
                       "extract_labels": float(np.mean(extract_ms))},
