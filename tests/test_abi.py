@@ -118,3 +118,45 @@ def test_tuned_options_always_fit(lib):
         p = gc.Params(w=w, h=h, D=D, tau=30, lam=10)
         o = autotune.tuned_opts(p)
         gc.gs_tile_info(p, o)          # raises if the shape does not fit
+
+
+def test_binding_refuses_host_tensors_and_bad_shapes(lib):
+    """The binding checks shapes, sizes, devices and dtypes before any device
+    call: a host tensor is refused (no CPU fallback), as are wrong sizes."""
+    import torch
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=64, h=8, D=4, tau=30, lam=2)
+    L = torch.zeros((8, 64), dtype=torch.uint8)
+    cost = torch.zeros(gc.gs_cost_volume_bytes(p) // 4, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        gc.gs_stereo_cost_volume(L, L, p, cost)                 # host tensors
+    with pytest.raises(ValueError):
+        gc.gs_stereo_cost_volume(L[:, :60], L, p, cost)         # wrong image shape
+    with pytest.raises(ValueError):
+        gc.gs_stereo_cost_volume(L, L, p, cost[:-1])            # wrong cost size
+    graph = torch.zeros(gc.gs_graph_bytes(p) - 1, dtype=torch.uint8)
+    status = torch.zeros(1, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        gc.gs_build_graph(cost, p, graph, status)               # graph too small
+    with pytest.raises(ValueError):
+        gc.gs_build_graph_skin(cost, p, torch.zeros((8, 3), dtype=torch.int32),
+                               torch.zeros((8, 3), dtype=torch.int32),
+                               torch.zeros(gc.gs_graph_bytes(p), dtype=torch.uint8), status)
+    with pytest.raises(ValueError):
+        gc.Batch([p] * 65, [gc.SolveOpts()] * 65)                # more than 64 pairs
+
+
+def test_params_and_options_pack_like_the_header(lib):
+    """ctypes mirrors of gs_params / gs_solve_opts / gs_pair_desc: sizes and
+    the defaults the Python dataclasses fill in."""
+    import ctypes
+    from paper_1803_01516_gb300 import gazecut as gc
+    assert ctypes.sizeof(gc.GsParams) == 9 * 4
+    assert ctypes.sizeof(gc.GsSolveOpts) == 48
+    p = gc.Params(w=100, h=10, D=8, tau=5, lam=3)
+    c = p.c()
+    assert (c.dis0, c.direction, c.inhibit, c.vertical_inhibit) == (14, 0, 1023, 1)
+    assert p.ng == 86
+    o = gc.SolveOpts().c()
+    assert (o.mode, o.engine, o.reserved, o.max_iters) == (gc.GS_MODE_EXACT, gc.GS_ENGINE_TILED,
+                                                           0, 1 << 16)
