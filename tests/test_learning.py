@@ -94,6 +94,87 @@ def test_adjoint_equals_difference_when_minimiser_unique():
     assert hits > 5
 
 
+def _tiny_images(rng, h=3, ng=3, D=3):
+    """Random uint8 images for h x ng sites and D depth numbers (dis0 = 2(D-1)),
+    values in 0..60: every feature is then at most 60, so a step of 1/256 in w1
+    or 2/256 in w2 moves a cost below tau by less than half a unit and never
+    across tau (costs at w1 = w2 = 1 are multiples of 1/2, tau is an integer)."""
+    w = 2 * (D - 1) + ng
+    L = rng.integers(0, 61, size=(h, w)).astype(np.uint8)
+    R = rng.integers(0, 61, size=(h, w)).astype(np.uint8)
+    return L, R
+
+
+def test_cost_grad_sums_equal_exact_finite_differences():
+    """cost_grad_sums against finite differences of the oracle's E* where the
+    minimiser is unique on both sides of the step (brute force over all 3^9
+    labelings): scaled by 256 the costs change exactly by the summed features,
+        E*(w1 + 1/256) - E*(w1)   = sums[0]           (sum |L-R| [c < tau])
+        E*(w2 + 2/256) - E*(w2)   = sums[1]           (sum 2|dxL-dxR| [c < tau])
+        E*(tau) - E*(tau - 1/256) = sums[2]           (sum [c >= tau], left derivative)
+        E*(tau + 1/256) - E*(tau) <= sums[2]          (right derivative counts c > tau)
+    in units of 1/256 of the energy.  A dropped factor 2, a swapped feature or
+    [c <= tau] against [c < tau] fails one of them."""
+    rng = np.random.default_rng(77)
+    D, dis0, scale = 3, 4, 256.0
+    w1, w2, tau, lam, inh = 1.0, 1.0, 20.0, 6, 9
+    lam_i, inh_i = int(lam * scale), int(inh * scale)
+    hits = {"w1": 0, "w2": 0, "tau": 0, "tau_tie": 0}
+
+    def bf(L, R, a, b, t):
+        C = learned.cost_volume_f32(L, R, D, dis0, a, b, t, scale)
+        return small.brute_force(C, lam_i, inh_i, 1)
+
+    for _ in range(60):
+        L, R = _tiny_images(rng)
+        E0, X0, n0 = bf(L, R, w1, w2, tau)
+        if n0 != 1:
+            continue
+        s = learned.cost_grad_sums(L, R, D, dis0, w1, w2, tau, X0)
+        E, X, n = bf(L, R, w1 + 1 / scale, w2, tau)
+        if n == 1 and np.array_equal(X, X0):
+            assert E - E0 == s[0]
+            hits["w1"] += 1
+        E, X, n = bf(L, R, w1, w2 + 2 / scale, tau)
+        if n == 1 and np.array_equal(X, X0):
+            assert E - E0 == s[1]
+            hits["w2"] += 1
+        Em, Xm, nm = bf(L, R, w1, w2, tau - 1 / scale)
+        Ep, Xp, np_ = bf(L, R, w1, w2, tau + 1 / scale)
+        if nm == 1 and np.array_equal(Xm, X0):
+            assert E0 - Em == s[2]
+            hits["tau"] += 1
+            if np_ == 1 and np.array_equal(Xp, X0):
+                assert Ep - E0 <= s[2]
+                hits["tau_tie"] += int(Ep - E0 < s[2])    # a site with c == tau at X*
+    assert hits["w1"] >= 10 and hits["w2"] >= 10 and hits["tau"] >= 10, hits
+    assert hits["tau_tie"] >= 1, hits
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_cost_grad_sums_bracketed_at_any_minimiser(seed):
+    """E* is concave in w1, w2 and tau (a minimum of functions concave in each):
+    at the oracle's minimiser the backward difference is an upper and the
+    forward difference a lower bound of the chain-rule sums (no uniqueness
+    needed; 4 x 5 sites, 4 depth numbers, max-flow oracle)."""
+    rng = np.random.default_rng(300 + seed)
+    D, dis0, scale = 4, 6, 256.0
+    w1, w2, tau, lam, inh = 1.0, 1.0, 25.0, 5, 11
+    L, R = _tiny_images(rng, h=4, ng=5, D=D)
+
+    def Estar(a, b, t):
+        C = learned.cost_volume_f32(L, R, D, dis0, a, b, t, scale)
+        return oracle.solve(C, int(lam * scale), int(inh * scale), 1)
+
+    r0 = Estar(w1, w2, tau)
+    s = learned.cost_grad_sums(L, R, D, dis0, w1, w2, tau, r0["labels"])
+    E0 = r0["flow"]
+    for k, (dw1, dw2, dt, g) in enumerate([(1, 0, 0, s[0]), (0, 2, 0, s[1]), (0, 0, 1, s[2])]):
+        up = Estar(w1 + dw1 / scale, w2 + dw2 / scale, tau + dt / scale)["flow"] - E0
+        down = E0 - Estar(w1 - dw1 / scale, w2 - dw2 / scale, tau - dt / scale)["flow"]
+        assert up <= g <= down, (k, up, g, down)
+
+
 # -------------------------------------------------------------- GPU part ---
 
 torch = pytest.importorskip("torch")
