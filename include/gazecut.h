@@ -57,7 +57,8 @@ extern "C" {
 #define GS_OK            0
 #define GS_ERR_INVAL     1   /* bad argument; or a negative data cost seen on the device */
 #define GS_ERR_OVERFLOW  2   /* capacities / flow would not fit the int32 state */
-#define GS_ERR_TIMEOUT   3   /* max_iters reached before the cut was exact; state stays valid */
+#define GS_ERR_TIMEOUT   3   /* max_iters reached, or the idle limit ran out, before the cut was
+                                exact; the state stays a valid preflow and the solve resumes */
 #define GS_ERR_CUDA      4   /* a CUDA launch or copy failed */
 #define GS_ERR_LABELS    5   /* the cut was not one depth number per gaze line (internal check) */
 #define GS_ERR_TOO_LARGE 6   /* the problem needs more scratch than gs_noalloc_scratch_bytes() */
@@ -106,8 +107,18 @@ typedef struct gs_solve_opts {
                                     rows per tile (1..8); 0, 0: chosen by the library.
                                     A shape that does not fit shared memory is refused
                                     (GS_ERR_INVAL). */
-    int32_t reserved;            /* must be 0 */
+    int32_t idle_limit_us;       /* TILED: a block of the persistent launch that finds no
+                                    work for this long gives up, and the pairs still
+                                    running end with GS_ERR_TIMEOUT (state valid,
+                                    resumable); 0: 60 s.  In a batch the smallest
+                                    non-zero value among the descriptors applies. */
 } gs_solve_opts;
+
+/* Host-side check of solve options (the same checks gs_maxflow_solve and
+ * gs_solve_batched apply): GS_OK or GS_ERR_INVAL (unknown mode or engine,
+ * sweeps_per_relabel < 1, max_iters < 1, a negative count, fixed_sweeps < 0 in
+ * GS_MODE_FIXED_SWEEPS, idle_limit_us < 0). */
+GS_API int gs_check_solve_opts(const gs_solve_opts *o);
 
 /* Derived sizes (0 when the params are invalid). */
 GS_API int32_t gs_num_sites_w(const gs_params *p);           /* n_g = w - dis0 */
@@ -360,7 +371,12 @@ GS_API int64_t gs_kernel_launches(void);
  * share the one array (it keeps the last call's contents; the solve clears
  * what must start at zero), so calls that overlap on the GPU race: issue them
  * on one stream or serialise them.  gs_extract_labels still takes its own
- * workspace.
+ * workspace.  The solve's statistics land in the shared array too:
+ * gs_solve_stats has no workspace to read them from for this call, and the
+ * next call overwrites them.
+ *
+ * The graph must live on the current device (the device whose array and
+ * stream the call uses); the Python binding refuses a tensor on another one.
  */
 GS_API size_t gs_noalloc_scratch_bytes(void);
 GS_API int gs_maxflow_solve_noalloc(void *graph, const gs_params *p, const gs_solve_opts *o,

@@ -31,6 +31,19 @@ int make_geom(const gs_params *p, Geom *g) {
     return GS_OK;
 }
 
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 1;
+    return sms;
+}
+
+int grid_for(int64_t n, int per_sm) {
+    const int64_t b = (n + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)per_sm * device_sms()));
+}
+
 size_t graph_bytes(const Geom &g) {
     return 256 + 9 * (size_t)round_up(g.N, 64) * sizeof(int32_t);
 }
@@ -180,7 +193,7 @@ int gs_energy(const int32_t *cost, const int32_t *labels, const gs_params *p, in
     cudaStream_t st = (cudaStream_t)stream;
     GS_CUDA_TRY(cudaMemsetAsync(energy, 0, sizeof(int64_t), st));
     long long sites = (long long)g.ng * g.h;
-    int blocks = (int)std::min<long long>((sites + 255) / 256, 4 * 152);
+    const int blocks = grid_for(sites, 4);
     k_energy<<<blocks, 256, 0, st>>>(cost, labels, g.ng, g.h, g.D, g.lam, g.h2h, g.h2v,
                                      (unsigned long long *)energy);
     count_launches(1);
@@ -335,7 +348,7 @@ int gs_cost_volume_f32_backward(const uint8_t *L, const uint8_t *R, int32_t pitc
     cudaStream_t st = (cudaStream_t)stream;
     GS_CUDA_TRY(cudaMemsetAsync(sums, 0, 3 * sizeof(int64_t), st));
     const long long sites = (long long)g.ng * g.h;
-    const int blocks = (int)std::min<long long>((sites + 255) / 256, 4 * 152);
+    const int blocks = grid_for(sites, 4);
     k_cost_f32_backward<<<blocks, 256, 0, st>>>(L, R, pitch, p->w, g.ng, g.h, g.D, p->dis0, w1, w2,
                                                tau, labels, (unsigned long long *)sums);
     count_launches(1);
@@ -350,7 +363,7 @@ int gs_energy_backward(const int32_t *labels, const gs_params *p, float grad, fl
     cudaStream_t st = (cudaStream_t)stream;
     GS_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * sizeof(int64_t), st));
     const long long sites = (long long)g.ng * g.h;
-    const int blocks = (int)std::min<long long>((sites + 255) / 256, 16 * 152);
+    const int blocks = grid_for(sites, 16);
     k_energy_backward<<<blocks, 256, 0, st>>>(labels, g.ng, g.h, g.D, p->vertical_inhibit ? 1 : 0,
                                              grad, dcost, (unsigned long long *)counts);
     count_launches(1);
@@ -377,7 +390,7 @@ extern "C" int gs_cost_add_at_labels(int32_t *cost, const int32_t *labels, const
     Geom g;
     if (make_geom(p, &g) != GS_OK || !cost || !labels) return GS_ERR_INVAL;
     const long long sites = (long long)g.ng * g.h;
-    const int blocks = (int)std::min<long long>((sites + 255) / 256, 16 * 152);
+    const int blocks = grid_for(sites, 16);
     k_cost_add_at_labels<<<blocks, 256, 0, (cudaStream_t)stream>>>(cost, labels, sites, g.D, value);
     count_launches(1);
     GS_CUDA_TRY(cudaGetLastError());

@@ -338,10 +338,6 @@ __global__ void k_flow(const GraphHeader *hdr, const Ctrl *ctrl, int64_t *flow) 
 
 using namespace gs;
 
-static int grid_for(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
-}
 
 // Shared with solve.cu: run the global relabel to convergence (defined there).
 namespace gs {

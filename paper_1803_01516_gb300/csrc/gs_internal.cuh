@@ -105,6 +105,11 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
 
 // Validate params and fill the geometry.  Returns GS_OK or GS_ERR_INVAL.
 int make_geom(const gs_params *p, Geom *g);
+// Number of SMs of the current device (1 if the query fails).
+int device_sms();
+// Grid for a grid-stride kernel over n items with 256-thread blocks: enough
+// blocks for n, at most per_sm resident blocks on every SM of the device.
+int grid_for(int64_t n, int per_sm = 16);
 size_t graph_bytes(const Geom &g);
 size_t work_bytes(const Geom &g);
 State state_view(void *graph, const Geom &g);

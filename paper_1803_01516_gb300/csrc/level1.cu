@@ -62,9 +62,7 @@ __global__ void k_skin_bounds(const int32_t *__restrict__ Xc, int ng, int h, int
     }
 }
 
-static int grid_sites(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
-}
+static int grid_sites(int64_t n) { return grid_for(n, 16); }
 
 }  // namespace gs
 

@@ -104,10 +104,6 @@ __global__ void k_sweep(Geom g, State s, Ctrl *ctrl) {
 
 __global__ void k_add_stat(Ctrl *ctrl, int which, long long v) { ctrl->stats[which] += v; }
 
-static int grid_for(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
-}
 
 int global_relabel(const Geom &g, const State &s, const Work &w, cudaStream_t st, int64_t *passes) {
     const int grid = grid_for(g.N);
@@ -158,16 +154,22 @@ struct PhaseTimer {
 
 using namespace gs;
 
+extern "C" int gs_check_solve_opts(const gs_solve_opts *o) {
+    if (!o) return GS_ERR_INVAL;
+    if (o->sweeps_per_relabel < 1 || o->max_iters < 1) return GS_ERR_INVAL;
+    if (o->engine != GS_ENGINE_TILED && o->engine != GS_ENGINE_SIMPLE) return GS_ERR_INVAL;
+    if (o->local_iters < 0 || o->relabel_passes < 0 || o->tail_iters < 0 || o->idle_limit_us < 0)
+        return GS_ERR_INVAL;
+    if (o->mode != GS_MODE_EXACT && o->mode != GS_MODE_FIXED_SWEEPS) return GS_ERR_INVAL;
+    if (o->mode == GS_MODE_FIXED_SWEEPS && o->fixed_sweeps < 0) return GS_ERR_INVAL;
+    return GS_OK;
+}
+
 extern "C" int gs_maxflow_solve(void *graph, const gs_params *p, const gs_solve_opts *o,
                                 void *workspace, int32_t *status, void *stream) {
     Geom g;
     if (make_geom(p, &g) != GS_OK || !o || !graph || !workspace || !status) return GS_ERR_INVAL;
-    if (o->sweeps_per_relabel < 1 || o->max_iters < 1) return GS_ERR_INVAL;
-    if (o->engine != GS_ENGINE_TILED && o->engine != GS_ENGINE_SIMPLE) return GS_ERR_INVAL;
-    if (o->reserved != 0 || o->local_iters < 0 || o->relabel_passes < 0 || o->tail_iters < 0)
-        return GS_ERR_INVAL;
-    if (o->mode != GS_MODE_EXACT && o->mode != GS_MODE_FIXED_SWEEPS) return GS_ERR_INVAL;
-    if (o->mode == GS_MODE_FIXED_SWEEPS && o->fixed_sweeps < 0) return GS_ERR_INVAL;
+    if (gs_check_solve_opts(o) != GS_OK) return GS_ERR_INVAL;
     if (((uintptr_t)workspace & 255) != 0) return GS_ERR_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     State s = state_view(graph, g);

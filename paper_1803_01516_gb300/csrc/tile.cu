@@ -769,7 +769,8 @@ struct PairCtl {
 };
 
 constexpr unsigned kItemMask = 0xffffffu;
-constexpr unsigned long long kIdleLimitNs = 60ull * 1000 * 1000 * 1000;   // an idle block gives up
+// An idle block gives up after this long unless the options set a limit.
+constexpr unsigned long long kDefaultIdleLimitNs = 60ull * 1000 * 1000 * 1000;
 
 static_assert(sizeof(PairState) % 8 == 0, "PairState is copied in 8-byte words");
 
@@ -789,6 +790,7 @@ __device__ __forceinline__ unsigned long long pack_claim(unsigned step, unsigned
 struct BatchArgs {
     int n;            // pairs
     int extract;      // 0: max-flow solve, 1: label extraction
+    unsigned long long idle_limit_ns;   // a block idle this long aborts the launch
     Ctrl *bar;        // abort flag and the count of finished pairs (Ctrl::active)
     PairCtl *ctl;     // [n]
     SolveArgs pair[kMaxPairs];
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                     got = 1;
                 }
                 if (!got) {
-                    if (now_ns() - t0 > kIdleLimitNs) {
+                    if (now_ns() - t0 > B.idle_limit_ns) {
                         atomicExch(&B.bar->abort, 1);
                         s_claim[3] = 1;
                         break;
@@ -1290,6 +1292,13 @@ static int launch_batch(const BatchArgs &B, int npt, size_t smem, int total_tile
 constexpr size_t kBatchCtrlBytes = 256 + kMaxPairs * sizeof(PairCtl);
 static_assert(256 + kBatchCtrlBytes <= kWorkCtrlBytes, "a pair's workspace holds a batch's control");
 
+// Idle limit of a launch from one pair's options (0: the default); a batch
+// takes the smallest.
+static unsigned long long idle_limit_ns(const gs_solve_opts *o) {
+    return o->idle_limit_us > 0 ? 1000ull * (unsigned long long)o->idle_limit_us
+                                : kDefaultIdleLimitNs;
+}
+
 static int run_batch(BatchArgs &B, int npt, size_t smem, void *ctrl_mem, cudaStream_t st) {
     B.bar = (Ctrl *)ctrl_mem;
     B.ctl = (PairCtl *)((char *)ctrl_mem + 256);
@@ -1309,6 +1318,7 @@ int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opt
     memset(&B, 0, sizeof(B));
     B.n = 1;
     B.extract = 0;
+    B.idle_limit_ns = idle_limit_ns(o);
     int npt;
     size_t smem;
     int rc = setup_args(g, s, w, o, B.pair[0], npt, smem);
@@ -1327,6 +1337,7 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
     memset(&B, 0, sizeof(B));
     B.n = 1;
     B.extract = 1;
+    B.idle_limit_ns = idle_limit_ns(o);
     int npt;
     size_t smem;
     int rc = setup_args(g, s, w, o, B.pair[0], npt, smem);
@@ -1378,6 +1389,7 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
     B.n = E.n = n;
     B.extract = 0;
     E.extract = 1;
+    B.idle_limit_ns = kDefaultIdleLimitNs;
     int npt_max = 4;
     size_t smem_max = 0;
     for (int i = 0; i < n; i++) {
@@ -1386,9 +1398,10 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
         if (make_geom(&d.p, &g) != GS_OK || !d.L || !d.R || !d.cost || !d.graph || !d.workspace ||
             !d.labels || !d.flow || !d.status)
             return GS_ERR_INVAL;
-        if (d.o.engine != GS_ENGINE_TILED || d.o.sweeps_per_relabel < 1 || d.o.max_iters < 1 ||
-            d.o.reserved != 0 || ((uintptr_t)d.graph & 255) || ((uintptr_t)d.workspace & 255))
+        if (gs_check_solve_opts(&d.o) != GS_OK || d.o.engine != GS_ENGINE_TILED ||
+            ((uintptr_t)d.graph & 255) || ((uintptr_t)d.workspace & 255))
             return GS_ERR_INVAL;
+        B.idle_limit_ns = std::min(B.idle_limit_ns, idle_limit_ns(&d.o));
         const State s = state_view(d.graph, g);
         const Work w = work_view(d.workspace, g);
         int npt;
@@ -1417,6 +1430,7 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
         if (rc) return rc;
         GS_CUDA_TRY(cudaMemsetAsync(B.pair[i].ctrl, 0, sizeof(Ctrl), st));
     }
+    E.idle_limit_ns = B.idle_limit_ns;
     int rc = run_batch(B, npt_max, smem_max, batch_ws, st);
     if (rc) return rc;
     return run_batch(E, npt_max, smem_max, batch_ws, st);

@@ -33,7 +33,7 @@ EXPORTS = [
     "gs_stereo_cost_volume_f32", "gs_energy_backward", "gs_cost_volume_f32_backward",
     "gs_cost_add_at_labels", "gs_batch_workspace_bytes", "gs_solve_batched",
     "gs_delegate_params", "gs_delegate_cost", "gs_skin_bounds", "gs_build_graph_skin",
-    "gs_build_graph_flags",
+    "gs_build_graph_flags", "gs_check_solve_opts",
 ]
 GS_BUILD_CHAIN_PREFLOW = 1
 
@@ -51,7 +51,7 @@ class GsSolveOpts(ctypes.Structure):
                 ("max_iters", ctypes.c_int64), ("local_iters", ctypes.c_int32),
                 ("relabel_passes", ctypes.c_int32), ("tail_iters", ctypes.c_int32),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("idle_limit_us", ctypes.c_int32)]
 
 
 class GsPairDesc(ctypes.Structure):
@@ -98,11 +98,12 @@ class SolveOpts:
     tail_iters: int = 0           # 0: library default
     tile_w: int = 0               # 0: library default
     tile_h: int = 0
+    idle_limit_us: int = 0        # 0: library default (60 s)
 
     def c(self) -> GsSolveOpts:
         return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, self.engine,
                            self.max_iters, self.local_iters, self.relabel_passes,
-                           self.tail_iters, self.tile_w, self.tile_h, 0)
+                           self.tail_iters, self.tile_w, self.tile_h, self.idle_limit_us)
 
 
 _lib = None
@@ -147,6 +148,7 @@ def lib():
             "gs_skin_bounds": ([P, pp, I32, P, P, P, P], ctypes.c_int),
             "gs_build_graph_skin": ([P, pp, P, P, P, P, P], ctypes.c_int),
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
+            "gs_check_solve_opts": ([po], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -168,6 +170,12 @@ def _dev(t: torch.Tensor, dtype, name: str):
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    # the library launches on the current device, with that device's stream
+    # (and, for the no-allocation solve, that device's static scratch)
+    cur = torch.cuda.current_device()
+    if t.device.index is not None and t.device.index != cur:
+        raise ValueError(f"{name} is on {t.device} but the current CUDA device is cuda:{cur}; "
+                         f"call inside torch.cuda.device({t.device.index})")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -468,9 +476,13 @@ class Batch:
             if L.shape != (p.h, p.w) or R.shape != (p.h, p.w):
                 raise ValueError(f"pair {i}: images must be [h, w]")
             arr[i] = GsPairDesc(p.c(), o.c(), _dev(L, torch.uint8, "L").value,
-                                _dev(R, torch.uint8, "R").value, b.cost.data_ptr(),
-                                b.graph.data_ptr(), b.work.data_ptr(), b.labels.data_ptr(),
-                                b.flow.data_ptr(), b.status.data_ptr())
+                                _dev(R, torch.uint8, "R").value,
+                                _dev(b.cost, torch.int32, "cost").value,
+                                _dev(b.graph, torch.uint8, "graph").value,
+                                _dev(b.work, torch.uint8, "workspace").value,
+                                _dev(b.labels, torch.int32, "labels").value,
+                                _dev(b.flow, torch.int64, "flow").value,
+                                _dev(b.status, torch.int32, "status").value)
         self._descs = arr       # keep alive
         return arr
 

@@ -158,5 +158,55 @@ def test_params_and_options_pack_like_the_header(lib):
     assert (c.dis0, c.direction, c.inhibit, c.vertical_inhibit) == (14, 0, 1023, 1)
     assert p.ng == 86
     o = gc.SolveOpts().c()
-    assert (o.mode, o.engine, o.reserved, o.max_iters) == (gc.GS_MODE_EXACT, gc.GS_ENGINE_TILED,
-                                                           0, 1 << 16)
+    assert (o.mode, o.engine, o.idle_limit_us, o.max_iters) == (gc.GS_MODE_EXACT,
+                                                                gc.GS_ENGINE_TILED, 0, 1 << 16)
+
+
+def test_solve_options_checked_alike_for_single_and_batched_solves(lib):
+    """gs_maxflow_solve and gs_solve_batched refuse the same bad options on the
+    host (one shared check, gs_check_solve_opts), before any device work."""
+    from paper_1803_01516_gb300 import gazecut as gc
+    good = gc.SolveOpts()
+    assert lib.gs_check_solve_opts(ctypes.byref(good.c())) == gc.GS_OK
+    bad = [gc.SolveOpts(mode=7), gc.SolveOpts(engine=3), gc.SolveOpts(sweeps_per_relabel=0),
+           gc.SolveOpts(max_iters=0), gc.SolveOpts(local_iters=-1), gc.SolveOpts(relabel_passes=-2),
+           gc.SolveOpts(tail_iters=-1), gc.SolveOpts(idle_limit_us=-5),
+           gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=-1)]
+    p = gc.Params(w=64, h=8, D=4, tau=30, lam=2)
+    fake = ctypes.c_void_p(256)
+    for o in bad:
+        oc = o.c()
+        assert lib.gs_check_solve_opts(ctypes.byref(oc)) == gc.GS_ERR_INVAL, o
+        assert lib.gs_maxflow_solve(fake, ctypes.byref(p.c()), ctypes.byref(oc), fake, fake,
+                                    None) == gc.GS_ERR_INVAL, o
+        d = gc.GsPairDesc(p.c(), oc, 256, 256, 256, 256, 256, 256, 256, 256)
+        arr = (gc.GsPairDesc * 1)(d)
+        assert lib.gs_solve_batched(ctypes.cast(arr, ctypes.c_void_p), 1, fake,
+                                    None) == gc.GS_ERR_INVAL, o
+
+
+def test_binding_refuses_a_tensor_on_another_device(lib, monkeypatch):
+    """The library launches on the current device (its stream, its static
+    scratch for the no-allocation solve): the binding refuses a tensor that
+    lives on another device instead of passing its pointer on.  A tensor that
+    only claims to be on cuda:1 (no storage, no GPU needed) stands in."""
+    import torch
+    from paper_1803_01516_gb300 import gazecut as gc
+
+    class OnDevice1(torch.Tensor):
+        @staticmethod
+        def __new__(cls, dtype):
+            return torch.Tensor._make_wrapper_subclass(cls, (16,), dtype=dtype,
+                                                       device=torch.device("cuda", 1))
+
+        @classmethod
+        def __torch_dispatch__(cls, func, types, args=(), kwargs=None):
+            raise RuntimeError("no compute on this stand-in")
+
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    p = gc.Params(w=64, h=8, D=4, tau=30, lam=2)
+    with pytest.raises(ValueError, match="current CUDA device"):
+        gc.gs_maxflow_solve_noalloc(OnDevice1(torch.uint8), p, gc.SolveOpts(),
+                                    OnDevice1(torch.int32))
+    with pytest.raises(ValueError, match="current CUDA device"):
+        gc.gs_energy(OnDevice1(torch.int32), OnDevice1(torch.int32), p, OnDevice1(torch.int64))
