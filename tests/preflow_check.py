@@ -96,3 +96,52 @@ def check_preflow(graph_bytes: np.ndarray, C: np.ndarray, lam: int, inhibit: int
     assert (ex[:, K - 1, :] >= -Ct[:, K, :]).all(), "sink capacity exceeded"
     used = int(Ct[:, K, :].sum() + np.minimum(ex[:, K - 1, :], 0).sum())
     return {"flow": used, "nodes": int(h * K * ng)}
+
+
+_SMIN = None
+
+
+def _smin_lib():
+    """Compile ``state_smin.c`` (plain gcc) next to this file, once."""
+    global _SMIN
+    if _SMIN is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "state_smin.c")
+        out_dir = os.path.join(here, "_build")
+        os.makedirs(out_dir, exist_ok=True)
+        lib = os.path.join(out_dir, "libstate_smin.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp,
+                                   src])
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        L.smin_labels.argtypes = [ctypes.c_void_p] + [ctypes.c_int64] * 6 + [ctypes.c_int,
+                                                                            ctypes.c_void_p]
+        L.smin_labels.restype = ctypes.c_int
+        _SMIN = L
+    return _SMIN
+
+
+def smin_labels(graph_bytes: np.ndarray, h: int, ng: int, D: int, lam: int, inhibit: int,
+                vinhibit: int) -> np.ndarray:
+    """Canonical (smallest-minimiser) labels read from a solved state: S_min by
+    reachability from the remaining excess, or for a label-reversed state the
+    mirrored largest minimiser from reachability to the remaining sink
+    capacity.  Raises AssertionError when a chain's side is not a prefix."""
+    import ctypes
+    K = D - 1
+    P = (ng + 31) // 32 * 32
+    N = h * K * P
+    stride = (N + 63) // 64 * 64
+    words = np.ascontiguousarray(graph_bytes[256:256 + 9 * stride * 4]).view(np.int32)
+    rev = int(graph_bytes[36:40].view(np.int32)[0])
+    ptrs = (ctypes.c_void_p * 9)(*[words[i * stride:].ctypes.data for i in range(9)])
+    X = np.zeros((h, ng), dtype=np.int32)
+    rc = _smin_lib().smin_labels(ptrs, h, ng, D, lam, inhibit, inhibit if vinhibit else 0, rev,
+                                 X.ctypes.data)
+    assert rc == 0, f"smin_labels failed (rc={rc})"
+    return X

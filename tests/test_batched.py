@@ -144,3 +144,59 @@ def test_full_batch_with_trivial_and_timed_out_pairs(gc):
         assert np.array_equal(b.labels.cpu().numpy(), ref["labels"]), i
         if i >= 60 and i < 63:
             assert ref["flow"] == 0
+
+
+def _golden_batch64():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "batch64_oracle.txt")
+    rows = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, w, h, D, sL, sR, flow, sX = line.split()
+        rows[int(k)] = (int(w), int(h), int(D), sL, sR, int(flow), sX)
+    return rows
+
+
+def _sha16(a):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()[:16]
+
+
+def test_batch_workload_of_64_pairs_matches_oracle_pair_by_pair(gc):
+    """The whole 64-pair batch workload (w ~ U[160, 640], h ~ U[120, 480],
+    16-64 depth numbers, 224 M graph nodes) in one batched call with the
+    autotuned options the bench uses: every pair's flow and labels equal the
+    CPU oracle's exact cut.  The oracle's results come from
+    golden/batch64_oracle.txt (written by golden/make_batch64_oracle.py, which
+    calls only the oracle: flow and a SHA-256 of the labels per pair); a pair
+    whose generated images hash differently on this machine is solved by the
+    oracle here instead."""
+    from paper_1803_01516_gb300 import autotune
+    gold = _golden_batch64()
+    batch = synth.make_batch(64)
+    same = [(gold[k][3], gold[k][4]) == (_sha16(L), _sha16(R))
+            for k, (_, L, R, _) in enumerate(batch)]
+    assert sum(not x for x in same) <= 4, "the generated inputs differ from the golden run"
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                        vertical_inhibit=1) for wl, _, _, _ in batch]
+    opts = [autotune.tuned_opts(p) for p in params]
+    B = gc.Batch(params, opts)
+    Ls = [torch.from_numpy(L).cuda() for _, L, _, _ in batch]
+    Rs = [torch.from_numpy(R).cuda() for _, _, R, _ in batch]
+    gc.gs_solve_batched(B, Ls, Rs)
+    torch.cuda.synchronize()
+    for k, ((wl, L, R, _), b) in enumerate(zip(batch, B.bufs)):
+        w, h, D, sL, sR, flow, sX = gold[k]
+        assert (w, h, D) == (wl.w, wl.h, wl.D), k
+        assert int(b.status.item()) == gc.GS_OK, k
+        X = b.labels.cpu().numpy().astype("<i4")
+        if same[k]:
+            assert int(b.flow.item()) == flow, k
+            assert _sha16(X) == sX, k
+        else:
+            C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+            ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+            assert int(b.flow.item()) == ref["flow"], k
+            assert np.array_equal(X, ref["labels"]), k

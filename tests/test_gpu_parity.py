@@ -170,6 +170,52 @@ def test_timeout_then_resume(gc, engine):
     assert np.array_equal(buf.labels.cpu().numpy(), ref["labels"])
 
 
+def test_idle_limit_runs_out_then_resume(gc):
+    """A caller-set idle limit is a bounded device-side wait that returns: with
+    a 1 us limit the blocks of the persistent launch that find no work give up
+    at once, the solve ends with GS_ERR_TIMEOUT and the state is still a valid
+    preflow; a second call with the default limit resumes it to the oracle's
+    exact cut (384x288, 16 depth numbers, hundreds of tiles)."""
+    from preflow_check import check_preflow
+    wl = synth.MAIN
+    L, R, _ = synth.make_pair(wl, 1)
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+    p = _params(gc, wl)
+    o = gc.SolveOpts(idle_limit_us=1)
+    buf = gc.Buffers(p, o)
+    gc.gs_build_graph(torch.from_numpy(C).cuda().reshape(-1), p, buf.graph, buf.status)
+    gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+    assert int(buf.status.item()) == gc.GS_ERR_TIMEOUT
+    check_preflow(buf.graph.cpu().numpy(), C, wl.lam, wl.inhibit, 1)
+    buf.status.zero_()
+    o2 = gc.SolveOpts()
+    gc.gs_maxflow_solve(buf.graph, p, o2, buf.work, buf.status)
+    gc.gs_extract_labels(buf.graph, p, o2, buf.work, buf.labels, buf.flow, buf.status)
+    assert int(buf.status.item()) == gc.GS_OK
+    assert int(buf.flow.item()) == ref["flow"]
+    assert np.array_equal(buf.labels.cpu().numpy(), ref["labels"])
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_fixed_sweeps_labels_valid_at_main_size(gc, direction):
+    """Fixed-sweep mode on the 384x288x16 pair: after 8, 32 and 128 sweep
+    rounds the labels are one depth number per gaze line (the cut is a cut),
+    the flow routed so far is a lower and the labels' energy an upper bound of
+    the exact minimum."""
+    wl = synth.MAIN
+    L, R, _ = synth.make_pair(wl, 2)
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    Estar = oracle.solve(C, wl.lam, wl.inhibit, 1)["flow"]
+    for n in (8, 32, 128):
+        o = gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=n, sweeps_per_relabel=8)
+        X, flow, status, _ = _solve_costs(gc, C, wl.lam, wl.inhibit, 1, o, direction)
+        assert status == gc.GS_OK
+        assert X.shape == (wl.h, C.shape[1]) and X.min() >= 0 and X.max() <= wl.D - 1
+        E = oracle.energy(C, X, wl.lam, wl.inhibit, 1)
+        assert flow <= Estar <= E
+
+
 def test_overflow_and_negative_cost_flagged(gc):
     p = gc.Params(w=20 + 6, h=4, D=4, tau=0, lam=1, inhibit=10)
     o = gc.SolveOpts()
