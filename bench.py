@@ -17,8 +17,14 @@ Extra keys on the JSON line:
   cpu_baseline  the CPU oracle (Boykov-Kolmogorov) on the bench's distinct pairs,
                 whose results also check the timed GPU results (parity_vs_oracle)
   clocks        SM clocks and throttle reasons sampled during the timed steps
-  batched       64 uneven pairs in one batched call (pairs/s) vs one call per pair
-  differentiated  forward exact solve + backward, 16 pairs at 384x288x32
+  batched       64 uneven pairs in one batched call replayed as a CUDA graph
+                (pairs/s) vs one call per pair
+  differentiated  forward exact solve + backward, 16 pairs at 384x288x32,
+                device-timed, next to the plain exact solve of the same pairs
+  learning      200 Adam steps on (w1, w2, tau, lambda) by the structured hinge
+                loss over 16 pairs at 384x288x32; Eq. 2 error before and after
+  fixed_sweeps  integer energy gap and ms of the fixed-sweep approximate mode
+  large         one 1920x1080x128 exact solve (228.5 M nodes) with its roofline
 
 --impl reference times the CPU oracle on the same workload (the reference arm).
 Multi-GPU (torchrun): replicas, each rank solves its own pairs; no collective
@@ -292,17 +298,33 @@ def _batched(gc, dev, args, stream, flush):
     B = gc.Batch(params, opts, device=dev)
     Ls = [torch.from_numpy(L).to(dev) for _, L, _, _ in batch]
     Rs = [torch.from_numpy(R).to(dev) for _, _, R, _ in batch]
-    gc.gs_solve_batched(B, Ls, Rs)                    # warm-up
+    gc.gs_solve_batched(B, Ls, Rs)                    # warm-up (and set-up outside capture)
     torch.cuda.synchronize(dev)
-    times = []
+    # the whole batched call captured once in a CUDA graph, then replayed
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            gc.gs_solve_batched(B, Ls, Rs)
+    stream.wait_stream(cap)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    times, times_uncaptured = [], []
     for i in range(args.batch_steps):
-        flush.fill_(i & 0xff)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        gc.gs_solve_batched(B, Ls, Rs)
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
+        for captured in (True, False):
+            flush.fill_(i & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if captured:
+                graph.replay()
+            else:
+                gc.gs_solve_batched(B, Ls, Rs)
+            b.record(stream)
+            b.synchronize()
+            (times if captured else times_uncaptured).append(a.elapsed_time(b))
+    graph.replay()
+    torch.cuda.synchronize(dev)
     ok = all(int(b.status.item()) == gc.GS_OK for b in B.bufs)
     flows = [int(b.flow.item()) for b in B.bufs]
     # the same pairs, one call each (same buffers, same options)
@@ -319,6 +341,8 @@ def _batched(gc, dev, args, stream, flush):
     nodes = sum(gc.gs_num_nodes(p) for p in params)
     out = {"pairs": len(params), "nodes": nodes, "ms_per_batch": float(np.mean(times)),
            "pairs_per_s": 1e3 * len(params) / float(np.mean(times)),
+           "timed_as": "replay of one CUDA graph holding the whole batched call",
+           "uncaptured_ms_per_batch": float(np.mean(times_uncaptured)),
            "single_call_loop_ms": t_single,
            "single_call_pairs_per_s": 1e3 * len(params) / t_single,
            "flows_match_single_calls": bool(ok),
@@ -339,13 +363,20 @@ def _batched(gc, dev, args, stream, flush):
     return out
 
 
+def _learned_workload():
+    return synth.Workload("learned-384x288x32", 384, 288, 32, tau=30, lam=8, sigma=2.0,
+                          scene="layers", n_layers=5, n_slanted=2, max_disp=31, seed_base=5)
+
+
 def _differentiated(gc, dev, args, stream):
     """Forward exact solve + backward on 16 pairs at 384x288 with 32 depth
-    numbers (learned FP32 data term, scale 256)."""
+    numbers (learned FP32 data term, scale 256), device-timed with CUDA
+    events around the whole loop (the forward never waits for the device; the
+    only host reads are the gradient transfers of the backward), next to the
+    plain exact solve of the same pairs and cost volumes (no gradient)."""
     import torch
     from paper_1803_01516_gb300 import learn
-    wl = synth.Workload("diff-384x288x32", 384, 288, 32, tau=30, lam=8, sigma=2.0, scene="layers",
-                        n_layers=5, n_slanted=2, max_disp=31, seed_base=5)
+    wl = _learned_workload()
     probs = []
     for i in range(args.diff_pairs):
         L, R, _ = synth.make_pair(wl, i)
@@ -354,15 +385,180 @@ def _differentiated(gc, dev, args, stream):
     theta = torch.tensor([1.0, 1.0, 30.0, 8.0], dtype=torch.float64, requires_grad=True)
     learn.min_energy(theta, probs[0]).backward()        # warm-up
     torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for pr in probs:
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    def fwd_bwd():
         theta.grad = None
-        learn.min_energy(theta, pr).backward()
-    torch.cuda.synchronize(dev)
-    dt = time.perf_counter() - t0
-    return {"pairs": len(probs), "ms_per_pair_fwd_bwd": 1e3 * dt / len(probs),
-            "pairs_per_s": len(probs) / dt,
+        E = sum(learn.min_energy(theta, pr) for pr in probs)
+        E.backward()
+
+    def plain():
+        for pr in probs:
+            learn.labels_at(theta, pr)
+
+    t_fb = min(timed(fwd_bwd) for _ in range(2))
+    t_plain = min(timed(plain) for _ in range(2))
+    for pr in probs:
+        pr.check()
+    n = len(probs)
+    return {"pairs": n, "ms_per_pair_fwd_bwd": t_fb / n, "pairs_per_s": 1e3 * n / t_fb,
+            "plain_exact_ms_per_pair": t_plain / n,
+            "backward_overhead": t_fb / t_plain - 1.0,
+            "timed_as": "CUDA events around all pairs (best of 2); forward = FP32 cost volume, "
+                        "graph, exact solve, labels, adjoint kernels; plain = the same without "
+                        "the adjoint",
             "workload": "384x288, 32 depth numbers, learned FP32 cost at scale 256"}
+
+
+def _learning(gc, dev, args):
+    """The learning workload: Adam on (w1, w2, tau, lambda) from (1, 1, 30, 8)
+    against the synthetic ground-truth depth of 16 pairs at 384x288x32 by the
+    structured hinge loss (exact loss-augmented cuts), theta projected to >= 0
+    after each step; Eq. 2 error and exact-site fraction before and after."""
+    import torch
+    from paper_1803_01516_gb300 import learn, metrics
+    wl = _learned_workload()
+    probs, gts, gts_np = [], [], []
+    for i in range(args.diff_pairs):
+        L, R, dR = synth.make_pair(wl, 100 + i)
+        p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=0, lam=0, inhibit=1023 * 256)
+        probs.append(learn.problem(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), p))
+        gt = metrics.gt_depth(dR, wl.D, 2 * (wl.D - 1))
+        gts_np.append(gt)
+        gts.append(torch.from_numpy(gt).to(dev))
+
+    def accuracy(theta):
+        err, exact, sites = 0, 0, 0
+        for pr, gt in zip(probs, gts_np):
+            X = learn.labels_at(theta, pr).cpu().numpy()
+            hist = metrics.depth_error_hist(X, gt)
+            err += metrics.depth_error_from_hist(hist)
+            exact += int(hist[0])
+            sites += int(hist.sum())
+        return {"eq2_error": err, "exact_fraction": exact / sites, "sites": sites}
+
+    theta0 = (1.0, 1.0, 30.0, 8.0)
+    before = accuracy(torch.tensor(theta0, dtype=torch.float64))
+    t0 = time.perf_counter()
+    theta, losses = learn.fit(theta0, probs, gts, steps=args.learn_steps, lr=args.learn_lr)
+    wall = time.perf_counter() - t0
+    after = accuracy(theta)
+    marks = sorted(set([0, len(losses) - 1] + list(range(0, len(losses), 20))))
+    return {"pairs": len(probs), "steps": len(losses), "optimizer": f"Adam lr={args.learn_lr}",
+            "theta0": {"w1": theta0[0], "w2": theta0[1], "tau": theta0[2], "lambda": theta0[3]},
+            "theta": dict(zip(["w1", "w2", "tau", "lambda"], [float(x) for x in theta])),
+            "hinge_loss": {str(k): losses[k] for k in marks},
+            "before": before, "after": after, "wall_s": wall,
+            "workload": "16 pairs at 384x288, 32 depth numbers (seeds disjoint from the "
+                        "differentiated leg), ground truth = the scene generator's depth"}
+
+
+def _fixed_sweeps(gc, dev, p, o, Ld, Rd, exact_flows, flush, stream):
+    """Fixed-sweep approximate mode on the main pairs: integer energy gap of its
+    labels against the exact minimum, and device ms of solve + labels."""
+    import torch
+    buf = gc.Buffers(p, o, device=dev)
+    E = torch.zeros(1, dtype=torch.int64, device=dev)
+    out = {}
+    for n in (8, 32, 128):
+        of = gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=n,
+                          sweeps_per_relabel=min(n, o.sweeps_per_relabel),
+                          local_iters=o.local_iters, relabel_passes=o.relabel_passes,
+                          tile_w=o.tile_w, tile_h=o.tile_h)
+        ms, gaps, rel, lows = [], [], [], []
+        for rep_ in range(2):
+            for k in range(len(Ld)):
+                gc.gs_stereo_cost_volume(Ld[k], Rd[k], p, buf.cost)
+                gc.gs_build_graph(buf.cost, p, buf.graph, buf.status)
+                flush.fill_(k & 0xff)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                gc.gs_maxflow_solve(buf.graph, p, of, buf.work, buf.status)
+                gc.gs_extract_labels(buf.graph, p, of, buf.work, buf.labels, buf.flow, buf.status)
+                c.record(stream)
+                gc.gs_energy(buf.cost, buf.labels, p, E)
+                c.synchronize()
+                if int(buf.status.item()) != gc.GS_OK:
+                    raise RuntimeError("fixed-sweep status")
+                if rep_ == 0:
+                    continue
+                ms.append(a.elapsed_time(c))
+                gap = int(E.item()) - exact_flows[k]
+                if gap < 0 or int(buf.flow.item()) > exact_flows[k]:
+                    raise RuntimeError("fixed-sweep bounds violated")
+                gaps.append(gap)
+                rel.append(gap / exact_flows[k])
+                lows.append((exact_flows[k] - int(buf.flow.item())) / exact_flows[k])
+        out[str(n)] = {"ms_per_pair": float(np.mean(ms)), "energy_gap_mean": float(np.mean(gaps)),
+                       "energy_gap_rel_mean": float(np.mean(rel)), "max_gap": int(max(gaps)),
+                       "flow_shortfall_rel_mean": float(np.mean(lows))}
+    return {"workload": "the main workload's pairs", "sweeps": out,
+            "gap": "E(labels) - exact min E (integer, >= 0); labels from the nodes that "
+                   "cannot reach remaining sink capacity"}
+
+
+def _large(gc, dev, flush, stream, peak):
+    """One 1920x1080 pair with 128 depth numbers (228.5 M graph nodes): device
+    time of each step of the path, solver statistics and the solve kernel's
+    algorithmic bytes against the HBM peak (the 8.2 GB state does not fit in
+    L2); flow == E(labels) checked on the device (the oracle cannot solve this
+    size; tests/test_large.py certifies it on the CPU)."""
+    import torch
+    from paper_1803_01516_gb300 import autotune
+    wl = synth.LARGE
+    L, R, _ = synth.make_pair(wl, 0)
+    p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                  vertical_inhibit=1)
+    o = autotune.tuned_opts(p)
+    buf = gc.Buffers(p, o, device=dev)
+    Ld, Rd = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
+    E = torch.zeros(1, dtype=torch.int64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    flush.fill_(1)
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    gc.gs_stereo_cost_volume(Ld, Rd, p, buf.cost)
+    gc.gs_build_graph(buf.cost, p, buf.graph, buf.status)
+    ev[1].record(stream)
+    gc.gs_maxflow_solve(buf.graph, p, o, buf.work, buf.status)
+    ev[2].record(stream)
+    gc.gs_extract_labels(buf.graph, p, o, buf.work, buf.labels, buf.flow, buf.status)
+    ev[3].record(stream)
+    gc.gs_energy(buf.cost, buf.labels, p, E)
+    ev[3].synchronize()
+    st = gc.gs_solve_stats(buf.work)
+    status = int(buf.status.item())
+    flow = int(buf.flow.item())
+    nodes = gc.gs_num_nodes(p)
+    ti = gc.gs_tile_info(p, o)
+    npt = nodes / ti["tiles"]
+    alg = (BYTES_PER_NODE_SWEEP * st["sweep_visits"] + BYTES_PER_NODE_BFS * st["relabel_visits"]) \
+        * npt
+    solve_ms = ev[1].elapsed_time(ev[2])
+    achieved = alg / (solve_ms * 1e-3) / 1e9
+    out = {"workload": wl.name, "nodes": nodes, "status": gc.STATUS_NAMES[status],
+           "ms_total": ev[0].elapsed_time(ev[3]),
+           "phases_ms": {"cost_volume+build": ev[0].elapsed_time(ev[1]), "maxflow_solve": solve_ms,
+                         "extract_labels": ev[2].elapsed_time(ev[3])},
+           "solver": {k: st[k] for k in ("relabels", "sweeps", "bfs_passes", "sweep_visits",
+                                          "relabel_visits")},
+           "tile": [ti["tile_w"], ti["tile_h"]],
+           "flow": flow, "flow_equals_energy_of_labels": flow == int(E.item()),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "alg_bytes": alg,
+                        "accounting": "72 B/node per tile visit of a sweep round + 40 B/node "
+                                      "per tile visit of a relabel pass"}}
+    del buf
+    torch.cuda.empty_cache()
+    return out
 
 
 def _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream, with_oracle):
@@ -609,8 +805,17 @@ def run(args):
         level1 = _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream,
                          not args.no_cpu_baseline)
         prepass = _prepass(gc, dev, p, o, Ld, Rd, flush, stream)
+    fixed = None
+    if not args.no_batched and world == 1:
+        fixed = _fixed_sweeps(gc, dev, p, o, Ld, Rd, exact_flows, flush, stream)
     batched = None if args.no_batched or world > 1 else _batched(gc, dev, args, stream, flush)
     diff = None if args.no_batched or world > 1 else _differentiated(gc, dev, args, stream)
+    large = None
+    if not args.no_large and world == 1:
+        large = _large(gc, dev, flush, stream, peak)
+    learning = None
+    if not args.no_learning and world == 1:
+        learning = _learning(gc, dev, args)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -637,6 +842,9 @@ def run(args):
         "batched": batched,
         "differentiated": diff,
         "level1_approximation": level1,
+        "fixed_sweeps": fixed,
+        "large": large,
+        "learning": learning,
         "initial_flow_prepass": prepass,
         "clocks": clk,
         "gpu_launches": int(launches),
@@ -665,6 +873,10 @@ def main():
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--diff-pairs", type=int, default=16)
+    ap.add_argument("--no-large", action="store_true", help="skip the 1920x1080x128 solve")
+    ap.add_argument("--no-learning", action="store_true", help="skip the learning run")
+    ap.add_argument("--learn-steps", type=int, default=200)
+    ap.add_argument("--learn-lr", type=float, default=0.1)
     ap.add_argument("--batched-cpu-baseline", action="store_true",
                     help="also time the CPU oracle on batch pairs (about a minute)")
     args = ap.parse_args()
