@@ -24,6 +24,7 @@ Extra keys on the JSON line:
   learning      200 Adam steps on (w1, w2, tau, lambda) by the structured hinge
                 loss over 16 pairs at 384x288x32; Eq. 2 error before and after
   fixed_sweeps  integer energy gap and ms of the fixed-sweep approximate mode
+  rgb_data_term the paper's colour data term on colour versions of the pairs
   large         one 1920x1080x128 exact solve (228.5 M nodes) with its roofline
 
 --impl reference times the CPU oracle on the same workload (the reference arm).
@@ -461,6 +462,54 @@ def _learning(gc, dev, args):
                         "differentiated leg), ground truth = the scene generator's depth"}
 
 
+def _rgb(gc, dev, flush, stream, with_oracle):
+    """The paper's colour data term (§4.3: |dR|+|dG|+|dB|, 0..765, no
+    truncation, lambda = 14) on colour versions of the main workload's pairs:
+    device ms of the whole path per pair, one pair checked against the oracle."""
+    import torch
+    from paper_1803_01516_gb300 import autotune
+    wl = synth.MAIN
+    p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=765, lam=14, inhibit=wl.inhibit,
+                  vertical_inhibit=1)
+    o = autotune.tuned_opts(p)
+    buf = gc.Buffers(p, o, device=dev)
+    pairs = [synth.make_pair_rgb(wl, i) for i in range(N_PAIRS)]
+    Ld = [torch.from_numpy(L).to(dev) for L, _, _ in pairs]
+    Rd = [torch.from_numpy(R).to(dev) for _, R, _ in pairs]
+    ms, cost_ms = [], []
+    for rep_ in range(3):
+        for k in range(N_PAIRS):
+            flush.fill_(k & 0xff)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            gc.gs_stereo_cost_volume_rgb(Ld[k], Rd[k], p, buf.cost)
+            ev[1].record(stream)
+            gc.solve_costs(buf.cost, p, o, buf)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            if int(buf.status.item()) != gc.GS_OK:
+                raise RuntimeError("rgb solve status")
+            if rep_:
+                ms.append(ev[0].elapsed_time(ev[2]))
+                cost_ms.append(ev[0].elapsed_time(ev[1]))
+    out = {"workload": "colour versions of the main workload's pairs (384x288x16), tau 765, "
+                       "lambda 14", "ms_per_pair": float(np.mean(ms)),
+           "cost_volume_ms": float(np.mean(cost_ms))}
+    if with_oracle:
+        import oracle
+        L, R, _ = pairs[0]
+        gc.gs_stereo_cost_volume_rgb(Ld[0], Rd[0], p, buf.cost)
+        gc.solve_costs(buf.cost, p, o, buf)
+        C = oracle.cost_volume_rgb(L, R, wl.D, 2 * (wl.D - 1), 765)
+        ref = oracle.solve(C, 14, wl.inhibit, 1)
+        out["parity_vs_oracle"] = {
+            "pairs_checked": 1,
+            "cost_volume_equal": bool(np.array_equal(buf.cost.cpu().numpy().reshape(C.shape), C)),
+            "flow_equal": int(buf.flow.item()) == ref["flow"],
+            "labels_equal": bool(np.array_equal(buf.labels.cpu().numpy(), ref["labels"]))}
+    return out
+
+
 def _fixed_sweeps(gc, dev, p, o, Ld, Rd, exact_flows, flush, stream):
     """Fixed-sweep approximate mode on the main pairs: integer energy gap of its
     labels against the exact minimum, and device ms of solve + labels."""
@@ -805,9 +854,10 @@ def run(args):
         level1 = _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream,
                          not args.no_cpu_baseline)
         prepass = _prepass(gc, dev, p, o, Ld, Rd, flush, stream)
-    fixed = None
+    fixed = rgb = None
     if not args.no_batched and world == 1:
         fixed = _fixed_sweeps(gc, dev, p, o, Ld, Rd, exact_flows, flush, stream)
+        rgb = _rgb(gc, dev, flush, stream, not args.no_cpu_baseline)
     batched = None if args.no_batched or world > 1 else _batched(gc, dev, args, stream, flush)
     diff = None if args.no_batched or world > 1 else _differentiated(gc, dev, args, stream)
     large = None
@@ -843,6 +893,7 @@ def run(args):
         "differentiated": diff,
         "level1_approximation": level1,
         "fixed_sweeps": fixed,
+        "rgb_data_term": rgb,
         "large": large,
         "learning": learning,
         "initial_flow_prepass": prepass,

@@ -132,9 +132,24 @@ GS_API int64_t gs_num_nodes(const gs_params *p);             /* graph nodes with
  *   cost[(y*n_g + W)*D + S] = min(|L[y*pitch + W+dis0-S] - R[y*pitch + W+S]|, tau)
  * L, R: uint8 images, row pitch `pitch` bytes (>= w).  cost: int32, layout
  * [h][n_g][D] (one contiguous depth chain per site), gs_cost_volume_bytes().
+ * Rows are staged with 128-bit loads when both images and the pitch are
+ * 16-byte aligned; no byte outside a row's first w is read.
  */
 GS_API int gs_stereo_cost_volume(const uint8_t *L, const uint8_t *R, int32_t pitch, const gs_params *p,
                           int32_t *cost, void *stream);
+
+/*
+ * Colour data term of §4.3, the form the paper uses:
+ *   cost[(y*n_g + W)*D + S] = min(|L_R - R_R| + |L_G - R_G| + |L_B - R_B|, tau)
+ * with (L_R, L_G, L_B) the left pixel (x_l, y) = (W+dis0-S, y) and
+ * (R_R, R_G, R_B) the right pixel (x_r, y) = (W+S, y); each sum lies in
+ * [0, 765], so tau >= 765 gives the paper's plain sum of absolute differences.
+ * L, R: interleaved 8-bit RGB (3 bytes per pixel, R first), row pitch `pitch`
+ * bytes (>= 3w); rows are staged with 128-bit loads when both images and the
+ * pitch are 16-byte aligned.  cost: layout and size as gs_stereo_cost_volume.
+ */
+GS_API int gs_stereo_cost_volume_rgb(const uint8_t *L, const uint8_t *R, int32_t pitch,
+                                     const gs_params *p, int32_t *cost, void *stream);
 
 /*
  * Chain graph of §3 / Fig. 4 (Ishikawa construction for the convex h~ of Eq. 1):

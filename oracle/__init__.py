@@ -7,7 +7,10 @@ the numpy part (``small.py``) are written from the paper's definitions alone.
 
 Functions (citations are to the paper):
 
-* ``cost_volume``   data term g_v at every cross point, §4.3 / §3
+* ``cost_volume``   data term g_v at every cross point, §4.3 / §3 (grayscale
+                    absolute difference, truncated)
+* ``cost_volume_rgb`` the paper's colour form of g_v, §4.3: the sum over R, G, B
+                    of the absolute differences (0..765), optionally truncated
 * ``solve``         exact min of E(X) (§2) by max-flow on the chain graph of
                     §3 / Fig. 4, with Boykov-Kolmogorov (§4.4) or Dinic;
                     returns flow, canonical labels X_min (smallest minimiser,
@@ -53,6 +56,8 @@ def _load():
         I = ctypes.c_int
         lib.or_cost_volume.argtypes = [P, P, I, I, I, I, I, P]
         lib.or_cost_volume.restype = I
+        lib.or_cost_volume_rgb.argtypes = [P, P, I, I, I, I, I, P]
+        lib.or_cost_volume_rgb.restype = I
         lib.or_energy.argtypes = [P, P, I, I, I, I, I, I]
         lib.or_energy.restype = ctypes.c_int64
         lib.or_solve.argtypes = [P, I, I, I, I, I, I, I, P, P, P, P]
@@ -80,6 +85,22 @@ def cost_volume(L: np.ndarray, R: np.ndarray, D: int, dis0: int, tau: int) -> np
     rc = lib.or_cost_volume(_ptr(L), _ptr(R), w, h, D, dis0, tau, _ptr(C))
     if rc:
         raise ValueError(f"or_cost_volume: bad sizes (rc={rc})")
+    return C
+
+
+def cost_volume_rgb(L: np.ndarray, R: np.ndarray, D: int, dis0: int, tau: int = 765) -> np.ndarray:
+    """C[y, W, S] = min(sum_c |L[y, W+dis0-S, c] - R[y, W+S, c]|, tau), int32 [h, n_g, D];
+    L, R uint8 [h, w, 3]."""
+    lib = _load()
+    L = np.ascontiguousarray(L, dtype=np.uint8)
+    R = np.ascontiguousarray(R, dtype=np.uint8)
+    assert L.ndim == 3 and L.shape[2] == 3 and R.shape == L.shape
+    h, w, _ = L.shape
+    ng = w - dis0
+    C = np.zeros((h, max(ng, 0), D), dtype=np.int32)
+    rc = lib.or_cost_volume_rgb(_ptr(L), _ptr(R), w, h, D, dis0, tau, _ptr(C))
+    if rc:
+        raise ValueError(f"or_cost_volume_rgb: bad sizes (rc={rc})")
     return C
 
 

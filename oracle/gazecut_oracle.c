@@ -55,6 +55,30 @@ int or_cost_volume(const uint8_t *L, const uint8_t *R, int w, int h, int D, int 
     return 0;
 }
 
+/* Colour data term of §4.3 at every cross point: the sum over the three
+ * channels of the absolute difference between left pixel (x_l, y) and right
+ * pixel (x_r, y), 0..765, then truncated at tau (tau >= 765: the paper's
+ * plain sum).  L, R: interleaved 8-bit RGB, h rows of w pixels (3w bytes). */
+int or_cost_volume_rgb(const uint8_t *L, const uint8_t *R, int w, int h, int D, int dis0,
+                       int tau, int32_t *C)
+{
+    int ng = w - dis0;
+    if (D < 2 || h < 1 || dis0 < 2 * (D - 1) || ng < 1) return 1;
+    for (int y = 0; y < h; y++)
+        for (int W = 0; W < ng; W++)
+            for (int S = 0; S < D; S++) {
+                const uint8_t *lp = L + ((size_t)y * w + (W + dis0 - S)) * 3;
+                const uint8_t *rp = R + ((size_t)y * w + (W + S)) * 3;
+                int sad = 0;
+                for (int c = 0; c < 3; c++) {
+                    int d = (int)lp[c] - (int)rp[c];
+                    sad += d < 0 ? -d : d;
+                }
+                C[((size_t)y * ng + W) * D + S] = sad < tau ? sad : tau;
+            }
+    return 0;
+}
+
 /* -------------------------------------------------------------- energy --- */
 
 static i64 pair_term(int a, int b, i64 lam, i64 inh)

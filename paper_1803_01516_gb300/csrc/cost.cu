@@ -70,36 +70,89 @@ Work work_view(void *ws, const Geom &g) {
     return w;
 }
 
+// Stage bytes [b0, b1) of an image row into shared memory (16-byte aligned
+// dst).  With `vec` (the row starts on a 16-byte boundary) the 16-byte chunks
+// from b0 rounded down that lie wholly inside the row's first row_end bytes
+// are copied with 128-bit loads and stores, and the bytes past the last such
+// chunk one at a time; nothing outside [0, row_end) is read.  Returns the
+// position of byte b0 in dst.
+__device__ __forceinline__ int stage_row(const uint8_t *__restrict__ row, int b0, int b1,
+                                         int row_end, uint8_t *dst, bool vec) {
+    if (!vec) {
+        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) dst[b - b0] = row[b];
+        return 0;
+    }
+    const int a0 = b0 & ~15;
+    const int vend = min((b1 + 15) & ~15, row_end & ~15);
+    const int chunks = vend > a0 ? (vend - a0) >> 4 : 0;
+    const uint4 *src = reinterpret_cast<const uint4 *>(row + a0);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) d[c] = __ldg(src + c);
+    for (int b = max(vend, a0) + threadIdx.x; b < b1; b += blockDim.x) dst[b - a0] = row[b];
+    return b0 - a0;
+}
+
+// Shared bytes for one staged span of n bytes (16-byte slack on each side).
+__host__ __device__ __forceinline__ int span_bytes(int n) { return (n + 47) & ~15; }
+
 // One block per (row y, tile of TW sites): the two image segments the tile
-// touches are staged in shared memory, then the [TW][D] output block, which is
-// contiguous in the cost volume, is written with coalesced stores.
+// touches are staged in shared memory (128-bit loads), then the [TW][D]
+// output block, which is contiguous in the cost volume, is written with
+// coalesced stores.
 constexpr int kCostTW = 64;
 
 __global__ void k_cost_volume(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R,
-                              int pitch, int ng, int D, int dis0, int tau,
+                              int pitch, int w, int ng, int D, int dis0, int tau, int vec,
                               int32_t *__restrict__ cost) {
-    extern __shared__ uint8_t sm[];
+    extern __shared__ __align__(16) uint8_t sm[];
     const int y = blockIdx.y;
     const int W0 = blockIdx.x * kCostTW;
     const int TW = min(kCostTW, ng - W0);
     const int span = TW + D - 1;
-    uint8_t *sL = sm;            // L[y][W0 + dis0 - (D-1) + t]
-    uint8_t *sR = sm + span;     // R[y][W0 + t]
-    const uint8_t *Lrow = L + (size_t)y * pitch + (W0 + dis0 - (D - 1));
-    const uint8_t *Rrow = R + (size_t)y * pitch + W0;
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
-        sL[t] = Lrow[t];
-        sR[t] = Rrow[t];
-    }
+    uint8_t *sL = sm;                         // L[y][W0 + dis0 - (D-1) + t]
+    uint8_t *sR = sm + span_bytes(span);      // R[y][W0 + t]
+    const int xl0 = W0 + dis0 - (D - 1);
+    const int oL = stage_row(L + (size_t)y * pitch, xl0, xl0 + span, w, sL, vec);
+    const int oR = stage_row(R + (size_t)y * pitch, W0, W0 + span, w, sR, vec);
     __syncthreads();
     int32_t *out = cost + ((size_t)y * ng + W0) * D;
     const int n = TW * D;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int w = e / D, S = e - w * D;
-        // x_l = W + dis0 - S  ->  sL index w + (D-1) - S ; x_r = W + S -> sR index w + S
-        int d = (int)sL[w + (D - 1) - S] - (int)sR[w + S];
+        const int wi = e / D, S = e - wi * D;
+        // x_l = W + dis0 - S  ->  sL index wi + (D-1) - S ; x_r = W + S -> sR index wi + S
+        int d = (int)sL[oL + wi + (D - 1) - S] - (int)sR[oR + wi + S];
         d = d < 0 ? -d : d;
         out[e] = d < tau ? d : tau;
+    }
+}
+
+// Colour data term of §4.3: sum over R, G, B of the absolute differences of
+// the left pixel (x_l, y) and the right pixel (x_r, y), interleaved 8-bit
+// RGB rows staged like the grayscale ones (3 bytes per pixel), truncated at
+// tau (tau >= 765 gives the paper's plain sum).
+__global__ void k_cost_volume_rgb(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R,
+                                  int pitch, int w, int ng, int D, int dis0, int tau, int vec,
+                                  int32_t *__restrict__ cost) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int y = blockIdx.y;
+    const int W0 = blockIdx.x * kCostTW;
+    const int TW = min(kCostTW, ng - W0);
+    const int span = 3 * (TW + D - 1);
+    uint8_t *sL = sm;
+    uint8_t *sR = sm + span_bytes(span);
+    const int xl0 = 3 * (W0 + dis0 - (D - 1));
+    const int oL = stage_row(L + (size_t)y * pitch, xl0, xl0 + span, 3 * w, sL, vec);
+    const int oR = stage_row(R + (size_t)y * pitch, 3 * W0, 3 * W0 + span, 3 * w, sR, vec);
+    __syncthreads();
+    int32_t *out = cost + ((size_t)y * ng + W0) * D;
+    const int n = TW * D;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int wi = e / D, S = e - wi * D;
+        const uint8_t *lp = sL + oL + 3 * (wi + (D - 1) - S);
+        const uint8_t *rp = sR + oR + 3 * (wi + S);
+        const int sad = abs((int)lp[0] - (int)rp[0]) + abs((int)lp[1] - (int)rp[1]) +
+                        abs((int)lp[2] - (int)rp[2]);
+        out[e] = sad < tau ? sad : tau;
     }
 }
 
@@ -172,15 +225,35 @@ int64_t gs_num_nodes(const gs_params *p) {
     return make_geom(p, &g) == GS_OK ? (int64_t)g.ng * g.h * g.K : 0;
 }
 
+// 128-bit staging needs both images and every row on a 16-byte boundary.
+static int rows_aligned(const uint8_t *L, const uint8_t *R, int32_t pitch) {
+    return (((uintptr_t)L | (uintptr_t)R) & 15) == 0 && (pitch & 15) == 0;
+}
+
 int gs_stereo_cost_volume(const uint8_t *L, const uint8_t *R, int32_t pitch, const gs_params *p,
                           int32_t *cost, void *stream) {
     Geom g;
     if (make_geom(p, &g) != GS_OK || !L || !R || !cost || pitch < p->w) return GS_ERR_INVAL;
     dim3 grid((g.ng + kCostTW - 1) / kCostTW, g.h);
-    size_t smem = 2 * (size_t)(kCostTW + g.D - 1);
+    const size_t smem = 2 * (size_t)span_bytes(kCostTW + g.D - 1);
     if (smem > 48 * 1024) return GS_ERR_INVAL;
-    k_cost_volume<<<grid, 256, smem, (cudaStream_t)stream>>>(L, R, pitch, g.ng, g.D, p->dis0,
-                                                             p->tau, cost);
+    k_cost_volume<<<grid, 256, smem, (cudaStream_t)stream>>>(
+        L, R, pitch, p->w, g.ng, g.D, p->dis0, p->tau, rows_aligned(L, R, pitch), cost);
+    count_launches(1);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int gs_stereo_cost_volume_rgb(const uint8_t *L, const uint8_t *R, int32_t pitch,
+                              const gs_params *p, int32_t *cost, void *stream) {
+    Geom g;
+    if (make_geom(p, &g) != GS_OK || !L || !R || !cost || pitch < 3 * (int64_t)p->w)
+        return GS_ERR_INVAL;
+    dim3 grid((g.ng + kCostTW - 1) / kCostTW, g.h);
+    const size_t smem = 2 * (size_t)span_bytes(3 * (kCostTW + g.D - 1));
+    if (smem > 48 * 1024) return GS_ERR_INVAL;
+    k_cost_volume_rgb<<<grid, 256, smem, (cudaStream_t)stream>>>(
+        L, R, pitch, p->w, g.ng, g.D, p->dis0, p->tau, rows_aligned(L, R, pitch), cost);
     count_launches(1);
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

@@ -33,7 +33,7 @@ EXPORTS = [
     "gs_stereo_cost_volume_f32", "gs_energy_backward", "gs_cost_volume_f32_backward",
     "gs_cost_add_at_labels", "gs_batch_workspace_bytes", "gs_solve_batched",
     "gs_delegate_params", "gs_delegate_cost", "gs_skin_bounds", "gs_build_graph_skin",
-    "gs_build_graph_flags", "gs_check_solve_opts",
+    "gs_build_graph_flags", "gs_check_solve_opts", "gs_stereo_cost_volume_rgb",
 ]
 GS_BUILD_CHAIN_PREFLOW = 1
 
@@ -149,6 +149,7 @@ def lib():
             "gs_build_graph_skin": ([P, pp, P, P, P, P, P], ctypes.c_int),
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
             "gs_check_solve_opts": ([po], ctypes.c_int),
+            "gs_stereo_cost_volume_rgb": ([P, P, I32, pp, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -214,6 +215,19 @@ def gs_stereo_cost_volume(L: torch.Tensor, R: torch.Tensor, p: Params, cost: tor
                                      ctypes.byref(p.c()), _dev(cost, torch.int32, "cost"),
                                      _stream(stream))
     _check(rc, "gs_stereo_cost_volume")
+
+
+def gs_stereo_cost_volume_rgb(L: torch.Tensor, R: torch.Tensor, p: Params, cost: torch.Tensor,
+                              stream=None):
+    """Colour data term (§4.3); L, R uint8 [h, w, 3] (interleaved RGB)."""
+    if L.shape != (p.h, p.w, 3) or R.shape != (p.h, p.w, 3):
+        raise ValueError("L, R must be [h, w, 3]")
+    if cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("cost has the wrong size")
+    rc = lib().gs_stereo_cost_volume_rgb(_dev(L, torch.uint8, "L"), _dev(R, torch.uint8, "R"),
+                                         3 * p.w, ctypes.byref(p.c()),
+                                         _dev(cost, torch.int32, "cost"), _stream(stream))
+    _check(rc, "gs_stereo_cost_volume_rgb")
 
 
 def gs_build_graph(cost: torch.Tensor, p: Params, graph: torch.Tensor, status: torch.Tensor,

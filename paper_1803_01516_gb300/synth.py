@@ -24,7 +24,8 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-__all__ = ["Workload", "TINY", "MAIN", "LARGE", "make_pair", "make_batch", "random_costs"]
+__all__ = ["Workload", "TINY", "MAIN", "LARGE", "make_pair", "make_pair_rgb", "make_batch",
+           "random_costs"]
 
 
 @dataclass(frozen=True)
@@ -125,6 +126,21 @@ def make_pair(wl: Workload, index: int = 0):
     xs = np.minimum(np.arange(wl.w)[None, :] + dR, wl.w - 1)
     R = np.take_along_axis(L, xs, axis=1).astype(np.float64)
     R = R + rng.normal(0.0, wl.sigma, size=R.shape)
+    R = np.clip(np.rint(R), 0, 255).astype(np.uint8)
+    return np.ascontiguousarray(L), np.ascontiguousarray(R), dR
+
+
+def make_pair_rgb(wl: Workload, index: int = 0):
+    """Colour version of ``make_pair``: the same scene recipe with an
+    independent texture per channel.  Returns (L, R, d_R) with L, R uint8
+    [h, w, 3] (interleaved R, G, B per pixel) and d_R int32 [h, w]."""
+    rng = np.random.default_rng(wl.seed_base * 1000 + 500 + index)
+    tex = rng.integers(0, 256, size=(3, wl.h, wl.w), dtype=np.int32).astype(np.uint8)
+    L = np.stack([_box_blur3(tex[c]) for c in range(3)], axis=-1)
+    dR = _layer_disparity(rng, wl)
+    xs = np.minimum(np.arange(wl.w)[None, :] + dR, wl.w - 1)
+    R = np.stack([np.take_along_axis(L[:, :, c], xs, axis=1) for c in range(3)], axis=-1)
+    R = R.astype(np.float64) + rng.normal(0.0, wl.sigma, size=R.shape)
     R = np.clip(np.rint(R), 0, 255).astype(np.uint8)
     return np.ascontiguousarray(L), np.ascontiguousarray(R), dR
 

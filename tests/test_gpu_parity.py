@@ -45,6 +45,74 @@ def test_cost_volume_bit_exact(gc, which):
     assert np.array_equal(cost.cpu().numpy().reshape(ref.shape), ref)
 
 
+def _offset_copy(a: np.ndarray, off: int):
+    """A device copy of `a` whose data starts `off` bytes past an allocation's
+    start (a view into a larger buffer): not 16-byte aligned when off % 16."""
+    flat = torch.zeros(a.size + off, dtype=torch.uint8, device="cuda")
+    flat[off:] = torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+    return flat[off:].view(*a.shape)
+
+
+@pytest.mark.parametrize("shape,off", [((48, 64), 0), ((33, 101), 0), ((20, 96), 3),
+                                       ((288, 384), 0)])
+def test_cost_volume_bit_exact_any_row_alignment(gc, shape, off):
+    """128-bit row staging (aligned images, pitch a multiple of 16) and the
+    byte path (odd pitch 101, or images starting 3 bytes past a boundary)
+    give the oracle's cost volume."""
+    h, w = shape
+    rng = np.random.default_rng(h * w + off)
+    L = rng.integers(0, 256, size=shape).astype(np.uint8)
+    R = rng.integers(0, 256, size=shape).astype(np.uint8)
+    for D in (2, 16, 23):
+        if w - 2 * (D - 1) < 1:
+            continue
+        p = gc.Params(w=w, h=h, D=D, tau=37, lam=1)
+        cost = torch.empty(gc.gs_cost_volume_bytes(p) // 4, dtype=torch.int32, device="cuda")
+        gc.gs_stereo_cost_volume(_offset_copy(L, off), _offset_copy(R, off), p, cost)
+        ref = oracle.cost_volume(L, R, D, 2 * (D - 1), 37)
+        assert np.array_equal(cost.cpu().numpy().reshape(ref.shape), ref), D
+
+
+@pytest.mark.parametrize("shape,off,tau", [((48, 64), 0, 765), ((33, 101), 0, 765),
+                                           ((20, 96), 5, 100), ((288, 384), 0, 765)])
+def test_rgb_cost_volume_bit_exact(gc, shape, off, tau):
+    """Colour data term of §4.3 (sum of |dR|+|dG|+|dB|, 0..765) on interleaved
+    RGB rows: aligned (128-bit staging), odd pitch 303 and misaligned images."""
+    h, w = shape
+    rng = np.random.default_rng(7 * h + w + off)
+    L = rng.integers(0, 256, size=(h, w, 3)).astype(np.uint8)
+    R = rng.integers(0, 256, size=(h, w, 3)).astype(np.uint8)
+    for D in (2, 16, 23):
+        if w - 2 * (D - 1) < 1:
+            continue
+        p = gc.Params(w=w, h=h, D=D, tau=tau, lam=1)
+        cost = torch.empty(gc.gs_cost_volume_bytes(p) // 4, dtype=torch.int32, device="cuda")
+        gc.gs_stereo_cost_volume_rgb(_offset_copy(L, off), _offset_copy(R, off), p, cost)
+        ref = oracle.cost_volume_rgb(L, R, D, 2 * (D - 1), tau)
+        assert np.array_equal(cost.cpu().numpy().reshape(ref.shape), ref), D
+
+
+@pytest.mark.parametrize("which", ["tiny", "main"])
+def test_rgb_pair_exact(gc, which):
+    """The colour pipeline end to end: RGB SAD data term (no truncation, the
+    paper's form), graph, exact solve, labels -- flow and labels equal the
+    oracle's on the colour version of the workload (lambda = 14, the paper's
+    best penalty for its colour data term)."""
+    wl = synth.TINY if which == "tiny" else synth.MAIN
+    L, R, _ = synth.make_pair_rgb(wl, 0)
+    p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=765, lam=14, inhibit=1023)
+    o = gc.SolveOpts()
+    buf = gc.Buffers(p, o)
+    gc.gs_stereo_cost_volume_rgb(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p,
+                                 buf.cost)
+    gc.solve_costs(buf.cost, p, o, buf)
+    C = oracle.cost_volume_rgb(L, R, wl.D, 2 * (wl.D - 1), 765)
+    ref = oracle.solve(C, 14, 1023, 1)
+    assert int(buf.status.item()) == gc.GS_OK
+    assert int(buf.flow.item()) == ref["flow"]
+    assert np.array_equal(buf.labels.cpu().numpy(), ref["labels"])
+
+
 ENGINES = [0, 1]   # tiled persistent, simple
 
 

@@ -269,3 +269,54 @@ def test_paper_table1_error_total():
     for d, n in rows:
         hist[d] = n
     assert depth_error_from_hist(hist) == 11578
+
+
+# ------------------------------------------------ colour data term (§4.3) ---
+
+def test_rgb_cost_of_gray_images_is_three_times_the_gray_cost():
+    """A grey image copied into all three channels: every channel contributes
+    the grey absolute difference, so the colour sum is three times it."""
+    L, R, _ = synth.make_pair(synth.TINY, 0)
+    L3, R3 = np.repeat(L[:, :, None], 3, axis=2), np.repeat(R[:, :, None], 3, axis=2)
+    C3 = oracle.cost_volume_rgb(L3, R3, 16, 30, 10 ** 6)
+    C1 = oracle.cost_volume(L, R, 16, 30, 10 ** 6)
+    assert np.array_equal(C3, 3 * C1)
+    # truncation applies to the sum
+    assert np.array_equal(oracle.cost_volume_rgb(L3, R3, 16, 30, 40), np.minimum(3 * C1, 40))
+
+
+def test_rgb_cost_range_channels_and_geometry():
+    """Black against white costs 765 (the paper's maximum); one differing
+    channel costs that channel's difference; permuting the channels of both
+    images changes nothing; the cross point (W, S) pairs left pixel
+    W + dis0 - S with right pixel W + S."""
+    h, w, D, dis0 = 2, 12, 3, 4
+    L = np.zeros((h, w, 3), np.uint8)
+    R = np.full((h, w, 3), 255, np.uint8)
+    assert (oracle.cost_volume_rgb(L, R, D, dis0, 10 ** 6) == 765).all()
+    R = L.copy()
+    R[:, :, 1] = 7
+    assert (oracle.cost_volume_rgb(L, R, D, dis0, 10 ** 6) == 7).all()
+    rng = np.random.default_rng(3)
+    L = rng.integers(0, 256, size=(h, w, 3)).astype(np.uint8)
+    R = rng.integers(0, 256, size=(h, w, 3)).astype(np.uint8)
+    C = oracle.cost_volume_rgb(L, R, D, dis0, 10 ** 6)
+    perm = [2, 0, 1]
+    assert np.array_equal(oracle.cost_volume_rgb(L[:, :, perm], R[:, :, perm], D, dis0, 10 ** 6), C)
+    for (y, W, S) in [(0, 0, 0), (1, 7, 2), (0, 3, 1)]:
+        want = int(np.abs(L[y, W + dis0 - S].astype(int) - R[y, W + S].astype(int)).sum())
+        assert C[y, W, S] == want
+
+
+def test_rgb_cost_zero_on_true_depth():
+    """Noise-free colour pair warped by a constant even disparity 2s: the
+    cross point at depth number D-1-s (dis = 2s) matches exactly."""
+    wl = synth.Workload("rgbflat", 40, 6, 5, tau=765, lam=1, sigma=0.0, scene="rects",
+                        rect_disps=(), max_disp=8)
+    L, _, _ = synth.make_pair_rgb(wl, 0)
+    for s in range(3):
+        d = 2 * s
+        R = np.concatenate([L[:, d:], L[:, -1:].repeat(d, axis=1)], axis=1) if d else L.copy()
+        C = oracle.cost_volume_rgb(L, R, 5, 8, 765)
+        S = 4 - s                                   # dis(S) = 8 - 2S = d
+        assert (C[:, :, S] == 0).all()
