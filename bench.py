@@ -25,6 +25,8 @@ Extra keys on the JSON line:
                 loss over 16 pairs at 384x288x32; Eq. 2 error before and after
   fixed_sweeps  integer energy gap and ms of the fixed-sweep approximate mode
   rgb_data_term the paper's colour data term on colour versions of the pairs
+  level1_approximation / level2_approximation  §4.5's approximate modes (ms,
+                energy gap against the exact minimum, oracle parity of one pair)
   large         one 1920x1080x128 exact solve (228.5 M nodes) with its roofline
 
 --impl reference times the CPU oracle on the same workload (the reference arm).
@@ -659,6 +661,55 @@ def _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream, with_oracle):
     return out
 
 
+def _level2(gc, dev, p, Ld, Rd, exact_flows, flush, stream, with_oracle, passes=2):
+    """Level-2 approximation (§4.5) on the main workload's pairs, block sizes 2
+    and 3: device time per pair from the images (cost volume, delegate cut,
+    skin, start labels, two passes of block cuts), energy gap against the
+    exact minimum, and one pair checked against the oracle."""
+    import torch
+    from paper_1803_01516_gb300 import autotune
+    out = {"workload": "the main workload's pairs", "passes": passes, "block_sizes": {}}
+    cost = torch.empty(gc.gs_cost_volume_bytes(p) // 4, dtype=torch.int32, device=dev)
+    E = torch.zeros(1, dtype=torch.int64, device=dev)
+    for b in (2, 3):
+        pc = gc.gs_delegate_params(p, b)
+        bufs = gc.Level1Buffers(p, b, autotune.tuned_opts(p), autotune.tuned_opts(pc), device=dev)
+        ms, gaps, rel = [], [], []
+        for rep_ in range(4):
+            for k in range(len(Ld)):
+                flush.fill_(k & 0xff)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                gc.gs_stereo_cost_volume(Ld[k], Rd[k], p, cost)
+                X, _, st = gc.solve_level2(cost, p, b, passes, bufs.o, bufs)
+                c.record(stream)
+                c.synchronize()
+                if int(st.item()) != gc.GS_OK:
+                    raise RuntimeError(f"level-2 status {int(st.item())}")
+                if rep_ == 0:
+                    continue
+                ms.append(a.elapsed_time(c))
+                gc.gs_energy(cost, X, p, E)
+                gap = int(E.item()) - exact_flows[k]
+                gaps.append(gap)
+                rel.append(gap / exact_flows[k])
+        entry = {"ms_per_pair": float(np.mean(ms)), "energy_gap_mean": float(np.mean(gaps)),
+                 "energy_gap_rel_mean": float(np.mean(rel)), "min_gap": int(min(gaps))}
+        if with_oracle:
+            import oracle
+            from oracle import level2 as l2
+            gc.gs_stereo_cost_volume(Ld[0], Rd[0], p, cost)
+            X, Xc, _ = gc.solve_level2(cost, p, b, passes, bufs.o, bufs)
+            C = cost.cpu().numpy().reshape(p.h, p.ng, p.D)
+            ref = l2.level2(C, p.lam, p.inhibit, 1, b, passes)
+            entry["parity_vs_oracle"] = {
+                "pairs_checked": 1,
+                "labels_equal": bool(np.array_equal(X.cpu().numpy(), ref["labels"])),
+                "coarse_labels_equal": bool(np.array_equal(Xc.cpu().numpy(), ref["coarse_labels"]))}
+        out["block_sizes"][str(b)] = entry
+    return out
+
+
 def _prepass(gc, dev, p, o, Ld, Rd, flush, stream):
     """Max-flow time with and without the chain-local initial flow (the
     build's stand-in for the paper's wave-front pre-pass), same pairs."""
@@ -844,7 +895,7 @@ def run(args):
             ok_lab &= bool(np.array_equal(buf.labels.cpu().numpy(), ref["labels"]))
         parity = {"pairs": len(refs), "flow_equal": ok_flow, "labels_equal": ok_lab}
 
-    level1 = prepass = None
+    level1 = level2 = prepass = None
     if not args.no_batched and world == 1:
         exact_flows = []
         for k in range(len(Ld)):
@@ -852,6 +903,8 @@ def run(args):
             torch.cuda.synchronize(dev)
             exact_flows.append(int(buf.flow.item()))
         level1 = _level1(gc, dev, p, Ld, Rd, exact_flows, flush, stream,
+                         not args.no_cpu_baseline)
+        level2 = _level2(gc, dev, p, Ld, Rd, exact_flows, flush, stream,
                          not args.no_cpu_baseline)
         prepass = _prepass(gc, dev, p, o, Ld, Rd, flush, stream)
     fixed = rgb = None
@@ -892,6 +945,7 @@ def run(args):
         "batched": batched,
         "differentiated": diff,
         "level1_approximation": level1,
+        "level2_approximation": level2,
         "fixed_sweeps": fixed,
         "rgb_data_term": rgb,
         "large": large,

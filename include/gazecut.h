@@ -358,6 +358,49 @@ GS_API int gs_skin_bounds(const int32_t *coarse_labels, const gs_params *p, int3
 GS_API int gs_build_graph_skin(const int32_t *cost, const gs_params *p, const int32_t *lo,
                                const int32_t *hi, void *graph, int32_t *status, void *stream);
 
+/*
+ * Level-2 hierarchical approximation (§4.5).  The paper's level 2 keeps the
+ * level-1 delegate cut and thin skin, but its push-relabel loop cuts each
+ * block separately while an undisclosed wave-front pass covers the skin as a
+ * whole.  This library fixes that reading as block-coordinate descent inside
+ * the skin:
+ *
+ *   start labels  each site's first argmin of the data term inside its
+ *                 delegate's depth bin [b Xc, min(b Xc + b, D) - 1]
+ *   block cut     block (bx, by) = sites W in [b bx, b bx + b), y in
+ *                 [b by, b by + b); with every other site held at its current
+ *                 label, the block's labels become the exact minimum of E (§2)
+ *                 inside lo <= X <= hi, canonical (smallest) minimiser; the
+ *                 pairs leaving the block act as data terms h~(l - X_u)
+ *   order         a pass cuts every block with (bx + by) even, then every
+ *                 block with (bx + by) odd against the new labels (blocks of
+ *                 one colour share no pair, so E never increases)
+ *
+ * A caller runs the level-1 steps up to gs_skin_bounds, then gs_level2_start
+ * on the delegate labels, then gs_block_descent.  The labels are read from
+ * `labels` (no flow value: the result is not a cut of the whole graph); its
+ * energy is gs_energy.
+ */
+
+/* Start labels (int32 [h][n_g], device) from the delegate labels (int32
+ * [h_c][n_gc], device) of block size b (1 <= b < D) over the data term cost.
+ * status: device int32[1], GS_ERR_LABELS when a delegate label is outside
+ * [0, D_c), else left as is. */
+GS_API int gs_level2_start(const int32_t *cost, const gs_params *p, int32_t b,
+                           const int32_t *coarse_labels, int32_t *labels, int32_t *status,
+                           void *stream);
+
+/* `passes` two-colour passes of exact block cuts (block size 1 <= b <= 3) on
+ * labels (int32 [h][n_g], device, updated in place; every label inside its
+ * bounds lo, hi on entry).  One warp solves a block by dynamic programming over
+ * row states, so a block's label range (the union of its sites' bounds) may
+ * hold at most min(3b, D) labels -- what gs_skin_bounds gives; a wider one
+ * sets GS_ERR_INVAL in status and leaves that block as it is.  2 passes = 4
+ * launches, stream-ordered, no host synchronisation. */
+GS_API int gs_block_descent(const int32_t *cost, const gs_params *p, int32_t b,
+                            const int32_t *lo, const int32_t *hi, int32_t *labels,
+                            int32_t passes, int32_t *status, void *stream);
+
 /* Tile shape the TILED engine uses for these params and options: host
  * int32[4] = {sites per tile along W, rows per tile, number of tiles, shared
  * bytes}.  GS_ERR_INVAL if the requested shape does not fit. */

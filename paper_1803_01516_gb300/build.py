@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgazecut.so")
-SOURCES = ["cost.cu", "graph.cu", "solve.cu", "tile.cu", "noalloc.cu", "level1.cu"]
+SOURCES = ["cost.cu", "graph.cu", "solve.cu", "tile.cu", "noalloc.cu", "level1.cu", "level2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-fvisibility=hidden", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -34,6 +34,7 @@ EXPORTS = [
     "gs_cost_add_at_labels", "gs_batch_workspace_bytes", "gs_solve_batched",
     "gs_delegate_params", "gs_delegate_cost", "gs_skin_bounds", "gs_build_graph_skin",
     "gs_build_graph_flags", "gs_check_solve_opts", "gs_stereo_cost_volume_rgb",
+    "gs_level2_start", "gs_block_descent",
 ]
 GS_BUILD_CHAIN_PREFLOW = 1
 
@@ -150,6 +151,8 @@ def lib():
             "gs_maxflow_solve_noalloc": ([P, pp, po, P, P], ctypes.c_int),
             "gs_check_solve_opts": ([po], ctypes.c_int),
             "gs_stereo_cost_volume_rgb": ([P, P, I32, pp, P, P], ctypes.c_int),
+            "gs_level2_start": ([P, pp, I32, P, P, P, P], ctypes.c_int),
+            "gs_block_descent": ([P, pp, I32, P, P, P, I32, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -392,6 +395,54 @@ def gs_build_graph_skin(cost: torch.Tensor, p: Params, lo: torch.Tensor, hi: tor
                                    _dev(graph, torch.uint8, "graph"),
                                    _dev(status, torch.int32, "status"), _stream(stream))
     _check(rc, "gs_build_graph_skin")
+
+
+# ------------------------------------------------ level-2 approximation ---
+
+def gs_level2_start(cost: torch.Tensor, p: Params, b: int, coarse_labels: torch.Tensor,
+                    labels: torch.Tensor, status: torch.Tensor, stream=None):
+    pc = gs_delegate_params(p, b)
+    if cost.numel() * 4 != gs_cost_volume_bytes(p) or coarse_labels.numel() != pc.ng * pc.h \
+            or labels.numel() != p.ng * p.h:
+        raise ValueError("cost / labels buffer has the wrong size")
+    rc = lib().gs_level2_start(_dev(cost, torch.int32, "cost"), ctypes.byref(p.c()), int(b),
+                               _dev(coarse_labels, torch.int32, "coarse_labels"),
+                               _dev(labels, torch.int32, "labels"),
+                               _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_level2_start")
+
+
+def gs_block_descent(cost: torch.Tensor, p: Params, b: int, lo: torch.Tensor, hi: torch.Tensor,
+                     labels: torch.Tensor, passes: int, status: torch.Tensor, stream=None):
+    if cost.numel() * 4 != gs_cost_volume_bytes(p):
+        raise ValueError("cost has the wrong size")
+    if lo.numel() != p.ng * p.h or hi.numel() != p.ng * p.h or labels.numel() != p.ng * p.h:
+        raise ValueError("bounds / labels must hold h * n_g entries")
+    rc = lib().gs_block_descent(_dev(cost, torch.int32, "cost"), ctypes.byref(p.c()), int(b),
+                                _dev(lo, torch.int32, "lo"), _dev(hi, torch.int32, "hi"),
+                                _dev(labels, torch.int32, "labels"), int(passes),
+                                _dev(status, torch.int32, "status"), _stream(stream))
+    _check(rc, "gs_block_descent")
+
+
+def solve_level2(cost: torch.Tensor, p: Params, b: int, passes: int = 2,
+                 o: SolveOpts | None = None, bufs: "Level1Buffers | None" = None, stream=None):
+    """Level-2 approximation of §4.5 from a cost volume int32 [h, n_g, D]:
+    delegate cut, thin skin, start labels, `passes` two-colour passes of exact
+    block cuts.  Returns (labels, coarse_labels, status) device tensors."""
+    o = o or SolveOpts()
+    bufs = bufs or Level1Buffers(p, b, o, device=cost.device)
+    c = cost.reshape(-1)
+    cb, fb = bufs.coarse, bufs.fine
+    gs_delegate_cost(c, p, b, cb.cost, bufs.status, stream)
+    gs_build_graph(cb.cost, bufs.pc, cb.graph, cb.status, stream)
+    gs_maxflow_solve(cb.graph, bufs.pc, bufs.oc, cb.work, cb.status, stream)
+    gs_extract_labels(cb.graph, bufs.pc, bufs.oc, cb.work, cb.labels, cb.flow, cb.status, stream)
+    gs_skin_bounds(cb.labels, p, b, bufs.lo, bufs.hi, bufs.status, stream)
+    gs_level2_start(c, p, b, cb.labels, fb.labels, bufs.status, stream)
+    gs_block_descent(c, p, b, bufs.lo, bufs.hi, fb.labels, passes, bufs.status, stream)
+    st = torch.where(bufs.status != 0, bufs.status, cb.status)
+    return fb.labels, cb.labels, st
 
 
 # ---------------------------------------------------------- whole pairs ---
