@@ -186,50 +186,60 @@ __device__ __forceinline__ int32_t smem_residual(const TileSmem &m, const TileGe
     }
 }
 
+// Fire-and-forget adds (PTX red): no result comes back, so a push does not
+// wait for the memory system before the next one.
+__device__ __forceinline__ void red_add_smem(int32_t *p, int32_t v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
+                 "r"(v));
+}
+__device__ __forceinline__ void red_add_gmem(int32_t *p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
 // Apply a push of d along slot q to the residual words in shared memory; when
 // the word belongs to a halo node (slots whose residual is stored at the arc's
 // head), the global copy is updated at once as well.  Only the data-arc
 // residual can grow without a bound of its own (flow pushed back along the
-// infinite reverse arc); its new value is returned for the overflow check.
-// Every other word is a residual of an arc pair and stays within the pair's
-// capacity, so those updates need no returned value.
-__device__ __forceinline__ int32_t smem_push_residual(const TileSmem &m, const TileGeom &t,
-                                                      const State &s, int pi, int64_t gi,
-                                                      const Geom &g, int q, int32_t d,
-                                                      bool head_is_halo) {
+// infinite reverse arc); it is checked for overflow when the tile is written
+// back.  Every other word is a residual of an arc pair and stays within the
+// pair's capacity.
+__device__ __forceinline__ void smem_push_residual(const TileSmem &m, const TileGeom &t,
+                                                   const State &s, int pi, int64_t gi,
+                                                   const Geom &g, int q, int32_t d,
+                                                   bool head_is_halo) {
     switch (q) {
-        case 0: atomicSub(&m.rc[pi], d); return 0;
-        case 1: return atomicAdd(&m.rc[pi - t.SJ], d) + d;   // chain never leaves the tile
-        case 2: atomicSub(&m.rr[pi], d); return 0;
+        case 0: red_add_smem(&m.rc[pi], -d); return;
+        case 1: red_add_smem(&m.rc[pi - t.SJ], d); return;   // chain never leaves the tile
+        case 2: red_add_smem(&m.rr[pi], -d); return;
         case 3:
-            if (head_is_halo) atomicAdd(&s.rr[gi - 1], d);
-            atomicAdd(&m.rr[pi - 1], d);
-            return 0;
-        case 4: atomicSub(&m.rd[pi], d); return 0;
+            if (head_is_halo) red_add_gmem(&s.rr[gi - 1], d);
+            red_add_smem(&m.rr[pi - 1], d);
+            return;
+        case 4: red_add_smem(&m.rd[pi], -d); return;
         case 5:
-            if (head_is_halo) atomicAdd(&s.rd[gi - g.SY], d);
-            atomicAdd(&m.rd[pi - t.SYs], d);
-            return 0;
-        case 6: atomicSub(&m.ri0[pi], d); return 0;
-        case 7: atomicSub(&m.ri1[pi], d); return 0;
-        case 8: atomicSub(&m.ri2[pi], d); return 0;
-        case 9: atomicSub(&m.ri3[pi], d); return 0;
+            if (head_is_halo) red_add_gmem(&s.rd[gi - g.SY], d);
+            red_add_smem(&m.rd[pi - t.SYs], d);
+            return;
+        case 6: red_add_smem(&m.ri0[pi], -d); return;
+        case 7: red_add_smem(&m.ri1[pi], -d); return;
+        case 8: red_add_smem(&m.ri2[pi], -d); return;
+        case 9: red_add_smem(&m.ri3[pi], -d); return;
         case 10:
-            if (head_is_halo) atomicAdd(&s.ri1[gi - 1 + g.P], d);
-            atomicAdd(&m.ri1[pi - 1 + t.SJ], d);
-            return 0;
+            if (head_is_halo) red_add_gmem(&s.ri1[gi - 1 + g.P], d);
+            red_add_smem(&m.ri1[pi - 1 + t.SJ], d);
+            return;
         case 11:
-            if (head_is_halo) atomicAdd(&s.ri0[gi + 1 + g.P], d);
-            atomicAdd(&m.ri0[pi + 1 + t.SJ], d);
-            return 0;
+            if (head_is_halo) red_add_gmem(&s.ri0[gi + 1 + g.P], d);
+            red_add_smem(&m.ri0[pi + 1 + t.SJ], d);
+            return;
         case 12:
-            if (head_is_halo) atomicAdd(&s.ri3[gi - g.SY + g.P], d);
-            atomicAdd(&m.ri3[pi - t.SYs + t.SJ], d);
-            return 0;
+            if (head_is_halo) red_add_gmem(&s.ri3[gi - g.SY + g.P], d);
+            red_add_smem(&m.ri3[pi - t.SYs + t.SJ], d);
+            return;
         default:
-            if (head_is_halo) atomicAdd(&s.ri2[gi + g.SY + g.P], d);
-            atomicAdd(&m.ri2[pi + t.SYs + t.SJ], d);
-            return 0;
+            if (head_is_halo) red_add_gmem(&s.ri2[gi + g.SY + g.P], d);
+            red_add_smem(&m.ri2[pi + t.SYs + t.SJ], d);
+            return;
     }
 }
 
@@ -246,57 +256,144 @@ __device__ __forceinline__ TileOrigin tile_origin(const TileGeom &t, int tile) {
     return o;
 }
 
-// Load the halo (one site around the tile, all layers) for the fields the
-// arcs of the tile's own nodes read: heights everywhere, and the residual
-// words stored at the head of an arc (rr, ri1 at W0-1; ri0 at W0+TW; rd, ri3
-// at y0-1; ri2 at y0+TH).  Positions outside the grid get height kInfH and
-// zero residuals.
-__device__ void load_halo(const SolveArgs &a, const TileSmem &m, const TileOrigin &o,
-                          bool with_residuals, const int32_t *hsrc) {
-    const Geom &g = a.g;
-    const TileGeom &t = a.t;
-    const State &s = a.s;
-    // left / right columns: TH * K each
-    for (int n = threadIdx.x; n < 2 * t.TH * g.K; n += blockDim.x) {
-        const int side = n / (t.TH * g.K);
-        const int r = n - side * t.TH * g.K;
-        const int yl = r / g.K, j = r - yl * g.K;
-        const int wl = side ? t.TW : -1;
-        const int W = o.W0 + wl, y = o.y0 + yl;
-        const int pi = pidx(t, yl, j, wl);
-        const bool in = W >= 0 && W < g.ng && y < g.h;
-        const int64_t gi = ((int64_t)y * g.K + j) * g.P + W;
-        m.ht[pi] = in ? ld(&hsrc[gi]) : kInfH;
-        if (with_residuals) {
-            if (side == 0) {
-                m.rr[pi] = in ? ld(&s.rr[gi]) : 0;
-                m.ri1[pi] = in ? ld(&s.ri1[gi]) : 0;
-            } else {
-                m.ri0[pi] = in ? ld(&s.ri0[gi]) : 0;
-            }
-        }
+// Staging with every global load issued before any shared-memory store: a
+// thread's first two halo cells go through registers (HaloRegs), so the halo
+// and the own nodes of a tile arrive in one round trip to L2 instead of one
+// per loop.  Cells past the first 2 x blockDim (large depth ranges) are
+// loaded afterwards by halo_rest.
+struct HaloRegs {
+    int32_t h[2], r1[2], r2[2];
+    int pi[2], kind[2];
+    bool ok[2];
+};
+
+// Halo cell n of the combined index space: the left and right columns
+// (2 TH K cells), then the top and bottom rows (2 K TW cells).  kind 0..3 =
+// left, right, top, bottom.
+__device__ __forceinline__ void halo_cell(const Geom &g, const TileGeom &t, const TileOrigin &o,
+                                          int n, int &pi, int64_t &gi, bool &in, int &kind) {
+    const int ncol = 2 * t.TH * g.K;
+    int yl, j, wl;
+    if (n < ncol) {
+        const int side = n / (t.TH * g.K), r = n - side * t.TH * g.K;
+        yl = r / g.K;
+        j = r - yl * g.K;
+        wl = side ? t.TW : -1;
+        kind = side;
+    } else {
+        n -= ncol;
+        const int side = n / (g.K * t.TW), r = n - side * g.K * t.TW;
+        j = r / t.TW;
+        wl = r - j * t.TW;
+        yl = side ? t.TH : -1;
+        kind = 2 + side;
     }
-    // top / bottom rows: K * TW each
-    for (int n = threadIdx.x; n < 2 * g.K * t.TW; n += blockDim.x) {
-        const int side = n / (g.K * t.TW);
-        const int r = n - side * g.K * t.TW;
-        const int j = r / t.TW, wl = r - j * t.TW;
-        const int yl = side ? t.TH : -1;
-        const int W = o.W0 + wl, y = o.y0 + yl;
-        const int pi = pidx(t, yl, j, wl);
-        const bool in = y >= 0 && y < g.h && W < g.ng;
-        const int64_t gi = ((int64_t)y * g.K + j) * g.P + W;
-        m.ht[pi] = in ? ld(&hsrc[gi]) : kInfH;
-        if (with_residuals) {
-            if (side == 0) {
-                m.rd[pi] = in ? ld(&s.rd[gi]) : 0;
-                m.ri3[pi] = in ? ld(&s.ri3[gi]) : 0;
-            } else {
-                m.ri2[pi] = in ? ld(&s.ri2[gi]) : 0;
-            }
+    const int W = o.W0 + wl, y = o.y0 + yl;
+    pi = pidx(t, yl, j, wl);
+    in = W >= 0 && W < g.ng && y >= 0 && y < g.h;
+    gi = ((int64_t)y * g.K + j) * g.P + W;
+}
+
+// Loads of a halo cell: the height, and the residual words stored at the head
+// of an arc of the tile's own nodes (rr, ri1 left; ri0 right; rd, ri3 top; ri2
+// bottom).  Positions outside the grid get height kInfH and zero residuals.
+__device__ __forceinline__ void halo_load(const SolveArgs &a, const int32_t *hsrc, bool with_res,
+                                          int64_t gi, bool in, int kind, int32_t &h, int32_t &r1,
+                                          int32_t &r2) {
+    const State &s = a.s;
+    h = in ? ld(&hsrc[gi]) : kInfH;
+    r1 = r2 = 0;
+    if (with_res && in) {
+        if (kind == 0) {
+            r1 = ld(&s.rr[gi]);
+            r2 = ld(&s.ri1[gi]);
+        } else if (kind == 1) {
+            r1 = ld(&s.ri0[gi]);
+        } else if (kind == 2) {
+            r1 = ld(&s.rd[gi]);
+            r2 = ld(&s.ri3[gi]);
+        } else {
+            r1 = ld(&s.ri2[gi]);
         }
     }
 }
+
+__device__ __forceinline__ void halo_store(const TileSmem &m, bool with_res, int pi, int kind,
+                                           int32_t h, int32_t r1, int32_t r2) {
+    m.ht[pi] = h;
+    if (!with_res) return;
+    if (kind == 0) {
+        m.rr[pi] = r1;
+        m.ri1[pi] = r2;
+    } else if (kind == 1) {
+        m.ri0[pi] = r1;
+    } else if (kind == 2) {
+        m.rd[pi] = r1;
+        m.ri3[pi] = r2;
+    } else {
+        m.ri2[pi] = r1;
+    }
+}
+
+__device__ __forceinline__ int halo_cells(const Geom &g, const TileGeom &t) {
+    return 2 * t.TH * g.K + 2 * g.K * t.TW;
+}
+
+__device__ __forceinline__ void halo_issue(const SolveArgs &a, const TileOrigin &o, bool with_res,
+                                           const int32_t *hsrc, HaloRegs &hr) {
+    const int total = halo_cells(a.g, a.t);
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int n = threadIdx.x + u * blockDim.x;
+        hr.ok[u] = n < total;
+        hr.pi[u] = 0;
+        hr.kind[u] = 0;
+        hr.h[u] = kInfH;
+        hr.r1[u] = hr.r2[u] = 0;
+        if (!hr.ok[u]) continue;
+        int64_t gi;
+        bool in;
+        halo_cell(a.g, a.t, o, n, hr.pi[u], gi, in, hr.kind[u]);
+        halo_load(a, hsrc, with_res, gi, in, hr.kind[u], hr.h[u], hr.r1[u], hr.r2[u]);
+    }
+}
+
+__device__ __forceinline__ void halo_commit(const TileSmem &m, bool with_res, const HaloRegs &hr) {
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+        if (hr.ok[u]) halo_store(m, with_res, hr.pi[u], hr.kind[u], hr.h[u], hr.r1[u], hr.r2[u]);
+}
+
+__device__ void halo_rest(const SolveArgs &a, const TileSmem &m, const TileOrigin &o,
+                          bool with_res, const int32_t *hsrc) {
+    const int total = halo_cells(a.g, a.t);
+    for (int n = threadIdx.x + 2 * blockDim.x; n < total; n += blockDim.x) {
+        int pi, kind;
+        int64_t gi;
+        bool in;
+        halo_cell(a.g, a.t, o, n, pi, gi, in, kind);
+        int32_t h, r1, r2;
+        halo_load(a, hsrc, with_res, gi, in, kind, h, r1, r2);
+        halo_store(m, with_res, pi, kind, h, r1, r2);
+    }
+}
+
+// Per-block tables of the tile shape of the pair a block is working on,
+// rebuilt only when the block moves to another pair (k_batch): for every own
+// position n of a tile its shared index and coordinates, packed as
+//   p (bits 0-12) | wl (13-17) | yl (18-20) | j (21-31)
+// (shared index < 8192: a tile's 9 fields fit the 180 KB budget; wl < 32,
+// yl < 8, j < 2048), and the per-slot push table of the sweep visits.  Visits
+// then need no division to place a node.
+__shared__ uint32_t s_info[kMaxTileNodes];
+
+__device__ __forceinline__ uint32_t pack_info(int p, int wl, int yl, int j) {
+    return (uint32_t)p | ((uint32_t)wl << 13) | ((uint32_t)yl << 18) | ((uint32_t)j << 21);
+}
+__device__ __forceinline__ int info_p(uint32_t v) { return (int)(v & 0x1fffu); }
+__device__ __forceinline__ int info_wl(uint32_t v) { return (int)((v >> 13) & 31u); }
+__device__ __forceinline__ int info_yl(uint32_t v) { return (int)((v >> 18) & 7u); }
+__device__ __forceinline__ int info_j(uint32_t v) { return (int)(v >> 21); }
 
 // Search direction of a relabel pass (see SolveArgs::dir).
 __device__ __forceinline__ int eff_dir(const SolveArgs &a) {
@@ -321,8 +418,12 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
     // warps update them.  Values only decrease and stay upper bounds, so any
     // interleaving converges to the same fixed point; an outer round in which
     // no height changed anywhere proves it has been reached.
+    // Neighbour heights are read with plain loads, all 14 at once (a missing
+    // arc reads the node's own height and is masked out), so they overlap:
+    // a height read stale inside a round only delays convergence, and the
+    // round that ends the loop changed nothing after fresh reads.
     constexpr int kInner = 4;
-    volatile int32_t *ht = m.ht;
+    int32_t *ht = m.ht;
     bool any_change = false;
     for (int outer = 0;; outer++) {
         int changed = 0;
@@ -333,15 +434,19 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
 #pragma unroll
             for (int k = 0; k < NPT; k++) {
                 if (pi[k] < 0) continue;
-                const int32_t h = ht[pi[k]];
+                const int p = pi[k];
+                const int32_t h = ht[p];
                 if (h == 0) continue;
+                const unsigned bits = mk[k];
+                int32_t hv[kSlots];
+#pragma unroll
+                for (int q = 0; q < kSlots; q++) hv[q] = ht[p + (((bits >> q) & 1u) ? off[q] : 0)];
                 int32_t hmin = kInfH;
-                const unsigned bits = mk[k] & 0x3fffu;
 #pragma unroll
                 for (int q = 0; q < kSlots; q++)
-                    if (bits & (1u << q)) hmin = min(hmin, ht[pi[k] + off[q]]);
+                    if ((bits >> q) & 1u) hmin = min(hmin, hv[q]);
                 if (hmin < kInfH && hmin + 1 < h) {
-                    ht[pi[k]] = hmin + 1;
+                    ht[p] = hmin + 1;
                     changed = 1;
                 }
             }
@@ -363,35 +468,56 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
     const int dir = eff_dir(a);
-    load_halo(a, m, o, true, a.hgt);
-    int pi[NPT];
+    HaloRegs hr;
+    halo_issue(a, o, true, a.hgt, hr);
+    int pi[NPT], pq[NPT];
     unsigned mk[NPT];
     int64_t gi[NPT];
+    int32_t v_rc[NPT], v_rr[NPT], v_rd[NPT], v_r0[NPT], v_r1[NPT], v_r2[NPT], v_r3[NPT], v_ex[NPT];
+    // own nodes: every load first ...
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
         const int n = threadIdx.x + k * blockDim.x;
-        pi[k] = -1;
+        pi[k] = pq[k] = -1;
         mk[k] = 0;
         gi[k] = 0;
+        v_rc[k] = v_rr[k] = v_rd[k] = v_r0[k] = v_r1[k] = v_r2[k] = v_r3[k] = v_ex[k] = 0;
         if (n >= t.TN) continue;
-        const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
+        const uint32_t info = s_info[n];
+        const int wl = info_wl(info), yl = info_yl(info), j = info_j(info);
         const int W = o.W0 + wl, y = o.y0 + yl;
-        const int p = pidx(t, yl, j, wl);
-        if (W >= g.ng || y >= g.h) {
+        pq[k] = info_p(info);
+        if (W >= g.ng || y >= g.h) continue;
+        const int64_t i = ((int64_t)y * g.K + j) * g.P + W;
+        pi[k] = pq[k];
+        gi[k] = i;
+        v_rc[k] = ld(&s.rc[i]);
+        v_rr[k] = ld(&s.rr[i]);
+        v_rd[k] = ld(&s.rd[i]);
+        v_r0[k] = ld(&s.ri0[i]);
+        v_r1[k] = ld(&s.ri1[i]);
+        v_r2[k] = ld(&s.ri2[i]);
+        v_r3[k] = ld(&s.ri3[i]);
+        v_ex[k] = ld(&s.ex[i]);
+    }
+    // ... then the shared-memory stores
+    halo_commit(m, true, hr);
+#pragma unroll
+    for (int k = 0; k < NPT; k++) {
+        if (pq[k] < 0) continue;
+        const int p = pq[k];
+        if (pi[k] < 0) {
             m.ht[p] = kInfH;
             continue;
         }
-        const int64_t i = ((int64_t)y * g.K + j) * g.P + W;
-        pi[k] = p;
-        gi[k] = i;
-        m.rc[p] = ld(&s.rc[i]);
-        m.rr[p] = ld(&s.rr[i]);
-        m.rd[p] = ld(&s.rd[i]);
-        m.ri0[p] = ld(&s.ri0[i]);
-        m.ri1[p] = ld(&s.ri1[i]);
-        m.ri2[p] = ld(&s.ri2[i]);
-        m.ri3[p] = ld(&s.ri3[i]);
-        const int32_t e = ld(&s.ex[i]);
+        m.rc[p] = v_rc[k];
+        m.rr[p] = v_rr[k];
+        m.rd[p] = v_rd[k];
+        m.ri0[p] = v_r0[k];
+        m.ri1[p] = v_r1[k];
+        m.ri2[p] = v_r2[k];
+        m.ri3[p] = v_r3[k];
+        const int32_t e = v_ex[k];
         if (dir == 0) {
             m.ht[p] = e < 0 ? 0 : kInfH;
             mk[k] = e > 0 ? 0x8000u : 0u;
@@ -399,13 +525,13 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
             m.ht[p] = e > 0 ? 0 : kInfH;
         }
     }
+    halo_rest(a, m, o, true, a.hgt);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
         if (pi[k] < 0) continue;
-        const int n = threadIdx.x + k * blockDim.x;
-        const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
-        const unsigned ex = arc_exists(g, o.y0 + yl, j, o.W0 + wl);
+        const uint32_t info = s_info[threadIdx.x + k * blockDim.x];
+        const unsigned ex = arc_exists(g, o.y0 + info_yl(info), info_j(info), o.W0 + info_wl(info));
 #pragma unroll
         for (int q = 0; q < kSlots; q++) {
             if (!((ex >> q) & 1u)) continue;
@@ -476,33 +602,37 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const TileOrigin o = tile_origin(t, tile);
-    load_halo(a, m, o, false, a.hgt);
-    int pi[NPT];
+    HaloRegs hr;
+    halo_issue(a, o, false, a.hgt, hr);
+    int pi[NPT], pq[NPT];
     unsigned mk[NPT];
     int64_t gi[NPT];
     int32_t h0[NPT];
+    // own nodes: every load first, then the shared-memory stores
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
         const int n = threadIdx.x + k * blockDim.x;
-        pi[k] = -1;
+        pi[k] = pq[k] = -1;
         mk[k] = 0;
         gi[k] = 0;
         h0[k] = kInfH;
         if (n >= t.TN) continue;
-        const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
+        const uint32_t info = s_info[n];
+        const int wl = info_wl(info), yl = info_yl(info), j = info_j(info);
         const int W = o.W0 + wl, y = o.y0 + yl;
-        const int p = pidx(t, yl, j, wl);
-        if (W >= g.ng || y >= g.h) {
-            m.ht[p] = kInfH;
-            continue;
-        }
+        pq[k] = info_p(info);
+        if (W >= g.ng || y >= g.h) continue;
         const int64_t i = ((int64_t)y * g.K + j) * g.P + W;
-        pi[k] = p;
+        pi[k] = pq[k];
         gi[k] = i;
         mk[k] = ld(&a.amask[i]);
         h0[k] = ld(&a.hgt[i]);
-        m.ht[p] = h0[k];
     }
+    halo_commit(m, false, hr);
+#pragma unroll
+    for (int k = 0; k < NPT; k++)
+        if (pq[k] >= 0) m.ht[pq[k]] = h0[k];
+    halo_rest(a, m, o, false, a.hgt);
     __shared__ int s_sides;
     if (threadIdx.x == 0) s_sides = 0;
     __syncthreads();
@@ -516,8 +646,8 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
         const int32_t h = m.ht[pi[k]];
         if (h != h0[k]) {
             __stcg(&a.hgt[gi[k]], h);
-            const int n = threadIdx.x + k * blockDim.x;
-            const int wl = n % t.TW, yl = (n / t.TW) / g.K;
+            const uint32_t info = s_info[threadIdx.x + k * blockDim.x];
+            const int wl = info_wl(info), yl = info_yl(info);
             sides |= (wl == 0 ? 1u : 0u) | (wl == t.TW - 1 ? 2u : 0u) | (yl == 0 ? 4u : 0u) |
                      (yl == t.TH - 1 ? 8u : 0u);
         }
@@ -538,6 +668,76 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
 
 // ------------------------------------------------------------ sweep visit ---
 
+// Per-slot push table of a tile shape, in shared memory: where a push along
+// slot q changes the residual word (shared offset from the node, its kind and
+// the pair capacity), where the head's excess lives (shared offset, global
+// offset), and where the word lives in global memory when the head is a halo
+// node.  A discharge then loops over a node's admissible slots only -- one or
+// two on average -- instead of running the code of all 14.
+//   .x  sword  shared offset of the residual word from the node (field * PN + off)
+//   .y  sex    shared offset of the head's excess
+//   .z  kind   0: word stored at the node (r = word, a push subtracts)
+//              1: word stored at the head (r = cap - word, a push adds)
+//              2: the infinite reverse data arc (a push adds to the head's rc)
+//   .w  cap    pair capacity of kind 1
+//   [1] .x dw, .y dy (head position in the tile), .z gfield (global array of
+//       the word: 0 rc .. 6 ri3), .w grel (global offset of the word)
+//   [2] .x gex (global offset of the head)
+struct SlotTab {
+    int4 a, b, c;
+};
+
+__device__ __forceinline__ SlotTab make_slot(const Geom &g, const TileGeom &t, int q) {
+    int dy, dj, dw;
+    slot_delta(q, dy, dj, dw);
+    const int off = dy * t.SYs + dj * t.SJ + dw;
+    // tile field order in shared memory: ht 0, ex 1, rc 2, rr 3, rd 4, ri0..ri3 5..8;
+    // in global memory: rc 0, rr 1, rd 2, ri0..ri3 3..6, ex 7, ht 8
+    int sfield, roff = 0, kind = 0, cap = 0, gfield = -1, grel = 0;
+    switch (q) {
+        case 0: sfield = 2; break;
+        case 1: sfield = 2; roff = -t.SJ; kind = 2; break;
+        case 2: sfield = 3; break;
+        case 3: sfield = 3; roff = -1; kind = 1; cap = g.lam2; gfield = 1; grel = -1; break;
+        case 4: sfield = 4; break;
+        case 5: sfield = 4; roff = -t.SYs; kind = 1; cap = g.lam2; gfield = 2; grel = -(int)g.SY; break;
+        case 6: sfield = 5; break;
+        case 7: sfield = 6; break;
+        case 8: sfield = 7; break;
+        case 9: sfield = 8; break;
+        case 10: sfield = 6; roff = -1 + t.SJ; kind = 1; cap = g.h2h; gfield = 4; grel = -1 + g.P; break;
+        case 11: sfield = 5; roff = 1 + t.SJ; kind = 1; cap = g.h2h; gfield = 3; grel = 1 + g.P; break;
+        case 12:
+            sfield = 8; roff = -t.SYs + t.SJ; kind = 1; cap = g.h2v; gfield = 6;
+            grel = -(int)g.SY + g.P;
+            break;
+        default:
+            sfield = 7; roff = t.SYs + t.SJ; kind = 1; cap = g.h2v; gfield = 5;
+            grel = (int)g.SY + g.P;
+            break;
+    }
+    SlotTab e;
+    e.a = make_int4(sfield * t.PN + roff, t.PN + off, kind, cap);
+    e.b = make_int4(dw, dy, gfield, grel);
+    e.c = make_int4((int)(dy * g.SY + (int64_t)dj * g.P + dw), 0, 0, 0);
+    return e;
+}
+
+__shared__ SlotTab s_slot[kSlots];
+
+// Fill the block's tables (s_info, s_slot) for the tile shape of pair a.
+__device__ void build_tables(const SolveArgs &a) {
+    const Geom &g = a.g;
+    const TileGeom &t = a.t;
+    for (int n = threadIdx.x; n < t.TN; n += blockDim.x) {
+        const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
+        s_info[n] = pack_info(pidx(t, yl, j, wl), wl, yl, j);
+    }
+    if (threadIdx.x < kSlots) s_slot[threadIdx.x] = make_slot(g, t, threadIdx.x);
+}
+
+
+
 // Up to local_iters push/relabel iterations of one tile in shared memory.
 template <int NPT>
 __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round, int iters,
@@ -549,55 +749,72 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     int32_t *act_next = a.tile_act + ((round + 1) & 1) * t.T;
     // per own node: shared index, coordinates in the tile and existing arcs,
     // so the discharge loop needs no divisions
-    __shared__ uint32_t s_info[kMaxTileNodes];
     __shared__ uint16_t s_exb[kMaxTileNodes];
-    load_halo(a, m, o, true, s.ht);
-    int pi[NPT];
+    HaloRegs hr;
+    halo_issue(a, o, true, s.ht, hr);
+    int pi[NPT], pq[NPT];
     int64_t gi[NPT];
-    unsigned ex_bits[NPT];
     int32_t o_ex[NPT], o_rc[NPT], o_rr[NPT], o_rd[NPT], o_r0[NPT], o_r1[NPT], o_r2[NPT],
         o_r3[NPT], o_ht[NPT];
+    // own nodes: every load first (the originals stay in registers for the
+    // write-back as deltas) ...
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
         const int n = threadIdx.x + k * blockDim.x;
-        pi[k] = -1;
+        pi[k] = pq[k] = -1;
         gi[k] = 0;
-        ex_bits[k] = 0;
+        o_ex[k] = o_rc[k] = o_rr[k] = o_rd[k] = o_r0[k] = o_r1[k] = o_r2[k] = o_r3[k] = 0;
+        o_ht[k] = kInfH;
         if (n >= t.TN) continue;
-        const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
+        const uint32_t info = s_info[n];
+        const int wl = info_wl(info), yl = info_yl(info), j = info_j(info);
         const int W = o.W0 + wl, y = o.y0 + yl;
-        const int p = pidx(t, yl, j, wl);
-        if (W >= g.ng || y >= g.h) {
+        pq[k] = info_p(info);
+        if (W >= g.ng || y >= g.h) continue;
+        const int64_t i = ((int64_t)y * g.K + j) * g.P + W;
+        pi[k] = pq[k];
+        gi[k] = i;
+        o_ex[k] = ld(&s.ex[i]);
+        o_ht[k] = ld(&s.ht[i]);
+        o_rc[k] = ld(&s.rc[i]);
+        o_rr[k] = ld(&s.rr[i]);
+        o_rd[k] = ld(&s.rd[i]);
+        o_r0[k] = ld(&s.ri0[i]);
+        o_r1[k] = ld(&s.ri1[i]);
+        o_r2[k] = ld(&s.ri2[i]);
+        o_r3[k] = ld(&s.ri3[i]);
+    }
+    // ... then the shared-memory stores
+    halo_commit(m, true, hr);
+#pragma unroll
+    for (int k = 0; k < NPT; k++) {
+        if (pq[k] < 0) continue;
+        const int p = pq[k];
+        if (pi[k] < 0) {
             m.ht[p] = kInfH;
             m.ex[p] = 0;
             continue;
         }
-        const int64_t i = ((int64_t)y * g.K + j) * g.P + W;
-        pi[k] = p;
-        gi[k] = i;
-        ex_bits[k] = arc_exists(g, y, j, W);
-        s_info[n] = (uint32_t)p | ((uint32_t)wl << 16) | ((uint32_t)yl << 21) | ((uint32_t)j << 25);
-        s_exb[n] = (uint16_t)ex_bits[k];
-        m.ex[p] = o_ex[k] = ld(&s.ex[i]);
-        m.ht[p] = o_ht[k] = ld(&s.ht[i]);
-        m.rc[p] = o_rc[k] = ld(&s.rc[i]);
-        m.rr[p] = o_rr[k] = ld(&s.rr[i]);
-        m.rd[p] = o_rd[k] = ld(&s.rd[i]);
-        m.ri0[p] = o_r0[k] = ld(&s.ri0[i]);
-        m.ri1[p] = o_r1[k] = ld(&s.ri1[i]);
-        m.ri2[p] = o_r2[k] = ld(&s.ri2[i]);
-        m.ri3[p] = o_r3[k] = ld(&s.ri3[i]);
+        const int n = threadIdx.x + k * blockDim.x;
+        const uint32_t info = s_info[n];
+        s_exb[n] = (uint16_t)arc_exists(g, o.y0 + info_yl(info), info_j(info), o.W0 + info_wl(info));
+        m.ex[p] = o_ex[k];
+        m.ht[p] = o_ht[k];
+        m.rc[p] = o_rc[k];
+        m.rr[p] = o_rr[k];
+        m.rd[p] = o_rd[k];
+        m.ri0[p] = o_r0[k];
+        m.ri1[p] = o_r1[k];
+        m.ri2[p] = o_r2[k];
+        m.ri3[p] = o_r3[k];
     }
+    halo_rest(a, m, o, true, s.ht);
     __syncthreads();
     int off[kSlots];
-    int64_t goff[kSlots];
 #pragma unroll
-    for (int q = 0; q < kSlots; q++) {
-        off[q] = soff(t, q);
-        int dy, dj, dw;
-        slot_delta(q, dy, dj, dw);
-        goff[q] = dy * g.SY + (int64_t)dj * g.P + dw;
-    }
+    for (int q = 0; q < kSlots; q++) off[q] = soff(t, q);
+    int32_t *const sbase = m.ht;                 // field f of the tile at sbase + f * PN
+    const int64_t gstride = s.rr - s.rc;         // global fields are equally spaced
     // Local iterations, one warp at a time and with no block barrier: each
     // warp compacts its own active nodes (positive excess, finite height; the
     // nodes its lanes own) into a warp list with ballots, discharges the list
@@ -627,9 +844,8 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
         for (int li = lane; li < cnt; li += 32) {
             const int n = wl_list[li];
             const uint32_t info = s_info[n];
-            const int p = (int)(info & 0xffffu);
-            const int wl = (int)((info >> 16) & 31u), yl = (int)((info >> 21) & 15u);
-            const int j = (int)(info >> 25);
+            const int p = info_p(info);
+            const int wl = info_wl(info), yl = info_yl(info), j = info_j(info);
             const int64_t gin = tile_g0 + (int64_t)yl * g.SY + (int64_t)j * g.P + wl;
             const unsigned exb = s_exb[n];
             const int32_t e = vex[p];
@@ -644,38 +860,46 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
                 rr[q] = ex ? smem_residual(m, t, g, p, q) : 0;
                 hv[q] = vht[p + (ex ? off[q] : 0)];
             }
-#pragma unroll
-            for (int q = 0; q < kSlots; q++)
-                if (rr[q] <= 0) hv[q] = kInfH;
-            int32_t left = e;
+            // residual and admissible slots as bit masks (registers only)
+            unsigned resid = 0, adm = 0;
 #pragma unroll
             for (int q = 0; q < kSlots; q++) {
-                if (left > 0 && rr[q] > 0 && hv[q] < hu) {
-                    const int32_t d = min(left, rr[q]);
-                    int dy, dj, dw;
-                    slot_delta(q, dy, dj, dw);
-                    const int wl2 = wl + dw, yl2 = yl + dy;
-                    const bool halo = wl2 < 0 || wl2 >= t.TW || yl2 < 0 || yl2 >= t.TH;
-                    const int32_t grown = smem_push_residual(m, t, s, p, gin, g, q, d, halo);
-                    overflow |= grown > kCapLimit;
-                    // an excess never exceeds the total source capacity (<= 2^30,
-                    // checked when the graph is built): no overflow check needed
-                    if (halo) {
-                        atomicAdd(&s.ex[gin + goff[q]], d);
-                        nb_touch |= wl2 < 0 ? 1u : wl2 >= t.TW ? 2u : yl2 < 0 ? 4u : 8u;
-                    } else {
-                        atomicAdd(&m.ex[p + off[q]], d);
-                    }
-                    rr[q] -= d;
-                    left -= d;
-                }
+                const bool rp = rr[q] > 0;
+                resid |= (unsigned)rp << q;
+                adm |= (unsigned)(rp && hv[q] < hu) << q;
             }
-            if (left != e) atomicSub(&m.ex[p], e - left);
+            int32_t left = e;
+            // push along the admissible slots, in slot order, until the
+            // excess is gone; the residual is re-read (it can only have grown)
+            for (unsigned bits = adm; bits && left > 0; bits &= bits - 1u) {
+                const int q = __ffs(bits) - 1;
+                const SlotTab st = s_slot[q];
+                int32_t *wp = sbase + p + st.a.x;
+                const int32_t w = *(volatile int32_t *)wp;
+                const int32_t r = st.a.z == 2 ? kInfR : st.a.z == 0 ? w : st.a.w - w;
+                const int32_t d = min(left, r);
+                if (d <= 0) continue;
+                red_add_smem(wp, st.a.z == 0 ? -d : d);
+                const int wl2 = wl + st.b.x, yl2 = yl + st.b.y;
+                if (wl2 < 0 || wl2 >= t.TW || yl2 < 0 || yl2 >= t.TH) {
+                    // the head is a halo node: its excess, and a word stored
+                    // at it, change in global memory at once
+                    if (st.a.z == 1) red_add_gmem(s.rc + st.b.z * gstride + gin + st.b.w, d);
+                    red_add_gmem(s.ex + gin + st.c.x, d);
+                    nb_touch |= wl2 < 0 ? 1u : wl2 >= t.TW ? 2u : yl2 < 0 ? 4u : 8u;
+                } else {
+                    red_add_smem(sbase + p + st.a.y, d);
+                }
+                left -= d;
+            }
+            if (left != e) red_add_smem(&m.ex[p], left - e);
             if (left > 0) {
+                // every admissible slot is saturated: relabel over the others
+                const unsigned rest = resid & ~adm;
                 int32_t hmin = kInfH;
 #pragma unroll
                 for (int q = 0; q < kSlots; q++)
-                    if (rr[q] > 0) hmin = min(hmin, hv[q]);
+                    if ((rest >> q) & 1u) hmin = min(hmin, hv[q]);
                 vht[p] = hmin >= kInfH - 1 ? kInfH : hmin + 1;
             }
         }
@@ -692,6 +916,10 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
         const int64_t i = gi[k];
         int32_t v;
         if ((v = m.ex[p] - o_ex[k])) atomicAdd(&s.ex[i], v);
+        // the data-arc residual is the one word that can grow without a bound
+        // of its own (flow pushed back down the infinite reverse arc); only
+        // this tile changes it (the chain stays inside the tile)
+        overflow |= m.rc[p] > kCapLimit || m.rc[p] < 0;
         if ((v = m.rc[p] - o_rc[k])) atomicAdd(&s.rc[i], v);
         if ((v = m.rr[p] - o_rr[k])) atomicAdd(&s.rr[i], v);
         if ((v = m.rd[p] - o_rd[k])) atomicAdd(&s.rd[i], v);
@@ -1019,6 +1247,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
     extern __shared__ int32_t smem[];
     __shared__ int s_claim[4];     // pair, item, step (low 32 bits), exit flag
     __shared__ PairState s_st;
+    int tables_for = -1;           // pair whose tile-shape tables the block holds
     // block 0 starts every pair and publishes its first step
     if (blockIdx.x == 0) {
         for (int p = threadIdx.x; p < B.n; p += blockDim.x) {
@@ -1094,6 +1323,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
         const int slot = (int)(step % 3), next = (int)((step + 1) % 3);
         PairCtl *c = B.ctl + pr;
         const SolveArgs &a = B.pair[pr];
+        if (pr != tables_for) {      // uniform: every thread read the same claim
+            build_tables(a);
+            tables_for = pr;
+            __syncthreads();
+        }
         const int phase = s_st.phase;
         const int T = a.t.T;
         const TileSmem m = tile_smem(smem, a.t.PN);
@@ -1198,7 +1432,11 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
             const int TN = TH * g.K * TW;
             const int PN = (TH + 2) * g.K * (TW + 2);
             const size_t bytes = 9 * (size_t)PN * sizeof(int32_t);
-            if (TN > max_nodes || TN > kMaxTileNodes || bytes > budget) continue;
+            // the packed node info holds shared indices below 8192 and depth
+            // layers below 2048
+            if (TN > max_nodes || TN > kMaxTileNodes || bytes > budget || PN >= 8192 ||
+                g.K >= 2048)
+                continue;
             t.TW = TW;
             t.TH = TH;
             t.PW = TW + 2;
