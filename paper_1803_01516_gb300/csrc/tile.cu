@@ -38,9 +38,11 @@ struct TileGeom {
     int TW, TH;        // sites per tile along W and y
     int PW;            // padded row length TW + 2
     int SJ;            // shared-memory stride of one chain layer (= PW)
-    int SYs;           // shared-memory stride of one row (= K * PW)
-    int PN;            // padded nodes per tile (TH + 2) * K * PW
+    int SYs;           // shared-memory stride of one row of sites: K * PW, padded
+                       // to SYs = TW (mod 32) when R > 0
+    int PN;            // padded nodes per tile (TH + 2) * SYs
     int TN;            // own nodes per tile TH * K * TW
+    int R;             // rows of sites one warp covers (32 / TW), 0: layers instead
     int tiles_w, tiles_h, T;
 };
 
@@ -730,7 +732,19 @@ __device__ void build_tables(const SolveArgs &a) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     for (int n = threadIdx.x; n < t.TN; n += blockDim.x) {
-        const int wl = n % t.TW, r = n / t.TW, j = r % g.K, yl = r / g.K;
+        int wl, yl, j;
+        if (t.R) {
+            // lanes: TW sites x R rows of one layer; then layers; then row groups
+            wl = n % t.TW;
+            const int u = (n / t.TW) % t.R, rest = n / (t.TW * t.R);
+            j = rest % g.K;
+            yl = (rest / g.K) * t.R + u;
+        } else {
+            wl = n % t.TW;
+            const int r = n / t.TW;
+            j = r % g.K;
+            yl = r / g.K;
+        }
         s_info[n] = pack_info(pidx(t, yl, j, wl), wl, yl, j);
     }
     if (threadIdx.x < kSlots) s_slot[threadIdx.x] = make_slot(g, t, threadIdx.x);
@@ -1430,7 +1444,16 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
         for (int ci = 0; ci < (want_w ? 1 : (int)(sizeof(cand) / sizeof(cand[0]))); ci++) {
             const int TW = want_w ? want_w : cand[ci][0], TH = want_w ? want_h : cand[ci][1];
             const int TN = TH * g.K * TW;
-            const int PN = (TH + 2) * g.K * (TW + 2);
+            // Bank-conflict-free placement: a warp takes the same TW sites in
+            // R = 32 / TW consecutive rows of sites (same layer), and the row
+            // stride is padded to TW (mod 32), so its 32 lanes touch 32
+            // different banks in every access of a visit (two rows of 16
+            // sites one layer apart, 18 words apart, shared two banks).
+            // Needs TH a multiple of R.
+            const int R = (TW < 32 && TH % (32 / TW) == 0) ? 32 / TW : 0;
+            int SYs = g.K * (TW + 2);
+            if (R) SYs += ((TW - SYs) % 32 + 32) % 32;
+            const int PN = (TH + 2) * SYs;
             const size_t bytes = 9 * (size_t)PN * sizeof(int32_t);
             // the packed node info holds shared indices below 8192 and depth
             // layers below 2048
@@ -1441,9 +1464,10 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
             t.TH = TH;
             t.PW = TW + 2;
             t.SJ = t.PW;
-            t.SYs = g.K * t.PW;
+            t.SYs = SYs;
             t.PN = PN;
             t.TN = TN;
+            t.R = R;
             t.tiles_w = (g.ng + TW - 1) / TW;
             t.tiles_h = (g.h + TH - 1) / TH;
             t.T = t.tiles_w * t.tiles_h;

@@ -144,6 +144,7 @@ def test_tiny_pair_exact(gc, vi, engine):
     ((9, 31, 12), 100, 1023, 1, 30),  # strong penalty: nearly constant labeling
     ((7, 45, 64), 3, 1023, 1, 30),    # long chains (D = 64)
     ((3, 21, 128), 2, 1023, 0, 40),   # D = 128, narrow tiles
+    ((2, 9, 200), 2, 1023, 1, 40),    # D = 200: depth layers past 7 bits of the node word
     ((11, 97, 16), 10, 1023, 1, 30),  # several tiles in both directions
 ])
 @pytest.mark.parametrize("engine", ENGINES)
