@@ -43,6 +43,8 @@ struct TileGeom {
     int PN;            // padded nodes per tile (TH + 2) * SYs
     int TN;            // own nodes per tile TH * K * TW
     int R;             // rows of sites one warp covers (32 / TW), 0: layers instead
+    int spread;        // R > 0: warp group g of the tile holds row group (g * spread) mod
+                       // (TN / 32), so a warp's groups lie far apart in the tile
     int tiles_w, tiles_h, T;
 };
 
@@ -734,11 +736,15 @@ __device__ void build_tables(const SolveArgs &a) {
     for (int n = threadIdx.x; n < t.TN; n += blockDim.x) {
         int wl, yl, j;
         if (t.R) {
-            // lanes: TW sites x R rows of one layer; then layers; then row groups
+            // lanes: TW sites x R rows of one layer; the warp group g = n / 32
+            // is placed at group (g * spread) mod M, M = TN / 32, numbered
+            // layer first, then row group
             wl = n % t.TW;
-            const int u = (n / t.TW) % t.R, rest = n / (t.TW * t.R);
-            j = rest % g.K;
-            yl = (rest / g.K) * t.R + u;
+            const int u = (n / t.TW) % t.R;
+            const int M = t.TN / 32;
+            const int gp = (int)(((long long)(n / 32) * t.spread) % M);
+            j = gp % g.K;
+            yl = (gp / g.K) * t.R + u;
         } else {
             wl = n % t.TW;
             const int r = n / t.TW;
@@ -1450,7 +1456,7 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
             // different banks in every access of a visit (two rows of 16
             // sites one layer apart, 18 words apart, shared two banks).
             // Needs TH a multiple of R.
-            const int R = (TW < 32 && TH % (32 / TW) == 0) ? 32 / TW : 0;
+            const int R = (TW <= 32 && TH % (32 / TW) == 0) ? 32 / TW : 0;
             int SYs = g.K * (TW + 2);
             if (R) SYs += ((TW - SYs) % 32 + 32) % 32;
             const int PN = (TH + 2) * SYs;
@@ -1468,6 +1474,25 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
             t.PN = PN;
             t.TN = TN;
             t.R = R;
+            // a multiplier near 0.618 M coprime with M: the groups a thread
+            // holds (32 x 16 nodes apart) map to spread-out parts of the tile,
+            // so a cluster of active nodes falls on many warps, not on one
+            t.spread = 1;
+            if (R) {
+                const int M = TN / 32;
+                for (int a = (int)(0.618 * M); a < 2 * M + 2; a++) {
+                    int x = a, y = M;
+                    while (y) {
+                        const int r = x % y;
+                        x = y;
+                        y = r;
+                    }
+                    if (a >= 1 && x == 1) {
+                        t.spread = a % M == 0 ? 1 : a;
+                        break;
+                    }
+                }
+            }
             t.tiles_w = (g.ng + TW - 1) / TW;
             t.tiles_h = (g.h + TH - 1) / TH;
             t.T = t.tiles_w * t.tiles_h;
