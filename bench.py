@@ -13,7 +13,9 @@ Extra keys on the JSON line:
                 bytes (72 B per node of every tile a sweep round visits, 40 B
                 per node of every tile a relabel pass visits) / its launch
                 time, measured with CUDA events on the solve's stream during
-                the timed steps, against the measured HBM copy bandwidth
+                the timed steps, against the L2-resident copy bandwidth
+                measured in the same run (the state fits in L2) and the
+                measured HBM copy bandwidth
   cpu_baseline  the CPU oracle (Boykov-Kolmogorov) on the bench's distinct pairs,
                 whose results also check the timed GPU results (parity_vs_oracle)
   clocks        SM clocks and throttle reasons sampled during the timed steps
@@ -89,6 +91,29 @@ def _profiled_traffic():
         return int(kv["traffic_bytes_per_launch"])
     except Exception:
         return None
+
+
+def _l2_copy_gbs(dev, mib: int = 32, reps: int = 200, trials: int = 5) -> float:
+    """Copy bandwidth of an L2-resident working set, measured here: a
+    `mib` MiB buffer copied into another (2 x 32 MiB, well under the 129 MB
+    L2) `reps` times back to back after a warm-up, CUDA events, best of
+    `trials`; read + write bytes."""
+    import torch
+    src = torch.empty(mib << 20, dtype=torch.uint8, device=dev)
+    dst = torch.empty_like(src)
+    src.fill_(1)
+    for _ in range(20):
+        dst.copy_(src)
+    best = 0.0
+    for _ in range(trials):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            dst.copy_(src)
+        b.record()
+        b.synchronize()
+        best = max(best, 2.0 * src.numel() * reps / (a.elapsed_time(b) * 1e-3) / 1e9)
+    return best
 
 
 def _peaks():
@@ -379,12 +404,14 @@ def _differentiated(gc, dev, args, stream):
     plain exact solve of the same pairs and cost volumes (no gradient)."""
     import torch
     from paper_1803_01516_gb300 import learn
+    from paper_1803_01516_gb300 import autotune
     wl = _learned_workload()
     probs = []
     for i in range(args.diff_pairs):
         L, R, _ = synth.make_pair(wl, i)
         p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=0, lam=0, inhibit=1023 * 256)
-        probs.append(learn.problem(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), p))
+        probs.append(learn.problem(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), p,
+                                   autotune.tuned_opts(p)))
     theta = torch.tensor([1.0, 1.0, 30.0, 8.0], dtype=torch.float64, requires_grad=True)
     learn.min_energy(theta, probs[0]).backward()        # warm-up
     torch.cuda.synchronize(dev)
@@ -428,12 +455,14 @@ def _learning(gc, dev, args):
     after each step; Eq. 2 error and exact-site fraction before and after."""
     import torch
     from paper_1803_01516_gb300 import learn, metrics
+    from paper_1803_01516_gb300 import autotune
     wl = _learned_workload()
     probs, gts, gts_np = [], [], []
     for i in range(args.diff_pairs):
         L, R, dR = synth.make_pair(wl, 100 + i)
         p = gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=0, lam=0, inhibit=1023 * 256)
-        probs.append(learn.problem(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), p))
+        probs.append(learn.problem(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), p,
+                                   autotune.tuned_opts(p)))
         gt = metrics.gt_depth(dR, wl.D, 2 * (wl.D - 1))
         gts_np.append(gt)
         gts.append(torch.from_numpy(gt).to(dev))
@@ -862,6 +891,7 @@ def run(args):
 
     # ----- roofline of the dominant kernel (the persistent solve) -----
     peak, peak_kind = _peaks()
+    l2_peak = _l2_copy_gbs(dev)
     nodes = gc.gs_num_nodes(p)
     ti = gc.gs_tile_info(p, o)
     nodes_per_tile = nodes / ti["tiles"]
@@ -880,7 +910,8 @@ def run(args):
         "relabel_passes": {"achieved": BYTES_PER_NODE_BFS * relabel_visits * nodes_per_tile
                            / max(relabel_ns, 1.0), "ms": relabel_ns * 1e-6}}
     for v in per_phase.values():
-        v["frac"] = v["achieved"] / peak
+        v["frac_l2"] = v["achieved"] / l2_peak
+        v["frac_hbm"] = v["achieved"] / peak
 
     # ----- CPU oracle on the same pairs: baseline time and parity of the timed pairs -----
     cpu = None
@@ -929,10 +960,16 @@ def run(args):
                                "replicas": world, "tile": [ti["tile_w"], ti["tile_h"]],
                                "direction": "auto"}),
         "e2e": e2e,
-        "roofline": {"bound": "hbm", "kernel": "k_batch (max-flow)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        # the 55 MB state of this workload stays in L2 (DRAM traffic per launch is a
+        # small fraction of the state, profiles/): L2 is the binding ceiling; the HBM
+        # copy peak is reported beside it
+        "roofline": {"bound": "l2", "kernel": "k_batch (max-flow)", "achieved": achieved,
+                     "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                      "traffic": _profiled_traffic(),
-                     "peak_kind": f"{peak_kind} HBM copy",
+                     "peak_kind": "measured in this run: L2-resident copy, 2 x 32 MiB, "
+                                  "best of 5 x 200 copies",
+                     "hbm": {"peak": peak, "frac": achieved / peak,
+                             "peak_kind": f"{peak_kind} HBM copy (MEASURED_PEAKS.json)"},
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": solve_s * 1e3,
                      "accounting": "72 B/node per tile visit of a sweep round + 40 B/node per "
                                    "tile visit of a relabel pass",

@@ -3,7 +3,8 @@
 What is tuned: the tile shape (sites per tile along W and y; every tile holds
 whole depth chains) and the schedule (sweep rounds between global relabels,
 local push/relabel iterations per tile visit, the pass cap of intermediate
-relabels).  A bucket is (depth numbers, log2 of the node count); its entry is
+relabels; an entry may add the local iterations of a tail visit as a sixth
+value).  A bucket is (depth numbers, log2 of the node count); its entry is
 measured on seeded synthetic pairs of that size (the same scene generator as
 the tests) with CUDA events, the best median over a few runs kept.
 
@@ -151,9 +152,10 @@ def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpt
         return gc.SolveOpts(**kw)
     best = entry["best"]
     spr, li, rp = best[:3]
-    tw, th = (best[3], best[4]) if len(best) == 5 else (0, 0)
+    tw, th = (best[3], best[4]) if len(best) >= 5 else (0, 0)
+    ti = best[5] if len(best) >= 6 else 0          # tail iterations (0: library default)
     o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
-                     tile_h=th, **kw)
+                     tile_h=th, tail_iters=ti, **kw)
     try:
         gc.gs_tile_info(p, o)
     except RuntimeError:

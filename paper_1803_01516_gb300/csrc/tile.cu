@@ -32,6 +32,7 @@
 namespace gs {
 
 constexpr int kTileThreads = 512;
+constexpr int kInitOuter = 2;                 // relaxation rounds of a first relabel pass
 constexpr int kMaxTileNodes = 4096;           // own nodes per tile (8 per thread at most)
 
 struct TileGeom {
@@ -412,7 +413,8 @@ __device__ __forceinline__ int eff_dir(const SolveArgs &a) {
 
 template <int NPT>
 __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi)[NPT],
-                           const unsigned (&mk)[NPT], int first_inner = 4) {
+                           const unsigned (&mk)[NPT], int first_inner = 4,
+                           int max_outer = 1 << 30) {
     const TileGeom &t = a.t;
     int off[kSlots];
 #pragma unroll
@@ -457,6 +459,7 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
         }
         if (!__syncthreads_or(changed)) break;
         any_change = true;
+        if (outer + 1 >= max_outer) break;
     }
     return any_change;
 }
@@ -567,7 +570,9 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
         m.ht[pidx(t, side ? t.TH : -1, j, wl)] = kInfH;
     }
     __syncthreads();
-    relax_tile<NPT>(a, m, pi, mk);
+    // the first pass's relaxation is capped: the pass after it visits every
+    // tile again, with the halo known, and relaxes each to its fixed point
+    relax_tile<NPT>(a, m, pi, mk, 4, kInitOuter);
     int act = 0;
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
@@ -770,6 +775,8 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     // per own node: shared index, coordinates in the tile and existing arcs,
     // so the discharge loop needs no divisions
     __shared__ uint16_t s_exb[kMaxTileNodes];
+    __shared__ unsigned s_touch;
+    if (threadIdx.x == 0) s_touch = 0;   // read only after the staging barrier below
     HaloRegs hr;
     halo_issue(a, o, true, s.ht, hr);
     int pi[NPT], pq[NPT];
@@ -950,11 +957,13 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
         if (m.ht[p] != o_ht[k]) __stcg(&s.ht[i], m.ht[p]);
         still |= m.ex[p] > 0 && m.ht[p] < kInfH;
     }
-    const int still_any = __syncthreads_or(still);
-    const unsigned touch = (unsigned)__syncthreads_or((int)(nb_touch & 1u)) |
-                           ((unsigned)__syncthreads_or((int)(nb_touch & 2u)) << 1) |
-                           ((unsigned)__syncthreads_or((int)(nb_touch & 4u)) << 2) |
-                           ((unsigned)__syncthreads_or((int)(nb_touch & 8u)) << 3);
+    // one barrier for the tile's flags: bits 0-3 neighbour tiles that received
+    // flow, bit 4 work left in this tile
+    const unsigned wbits = __reduce_or_sync(0xffffffffu, nb_touch | (still ? 16u : 0u));
+    if ((threadIdx.x & 31) == 0 && wbits) atomicOr(&s_touch, wbits);
+    __syncthreads();
+    const unsigned touch = s_touch;
+    const bool still_any = (touch & 16u) != 0;
     if (threadIdx.x < 4 && (touch >> threadIdx.x & 1u)) {
         const int nb = side_tile(t, o, tile, threadIdx.x);
         if (nb >= 0) enqueue(act_next, list_next, count_next, nb);
