@@ -772,15 +772,16 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
     int32_t *act_next = a.tile_act + ((round + 1) & 1) * t.T;
-    // per own node: shared index, coordinates in the tile and existing arcs,
-    // so the discharge loop needs no divisions
-    __shared__ uint16_t s_exb[kMaxTileNodes];
+    const int64_t tile_g0 = (int64_t)o.y0 * g.SY + o.W0;
     __shared__ unsigned s_touch;
     if (threadIdx.x == 0) s_touch = 0;   // read only after the staging barrier below
     HaloRegs hr;
     halo_issue(a, o, true, s.ht, hr);
-    int pi[NPT], pq[NPT];
-    int64_t gi[NPT];
+    // own node k of this thread: its packed position (s_info) and whether it
+    // lies inside the grid (bit k of vmask); positions past the tile's nodes
+    // are not in vmask either
+    uint32_t inf[NPT];
+    unsigned vmask = 0, tmask = 0;
     int32_t o_ex[NPT], o_rc[NPT], o_rr[NPT], o_rd[NPT], o_r0[NPT], o_r1[NPT], o_r2[NPT],
         o_r3[NPT], o_ht[NPT];
     // own nodes: every load first (the originals stay in registers for the
@@ -788,19 +789,18 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
         const int n = threadIdx.x + k * blockDim.x;
-        pi[k] = pq[k] = -1;
-        gi[k] = 0;
+        inf[k] = 0;
         o_ex[k] = o_rc[k] = o_rr[k] = o_rd[k] = o_r0[k] = o_r1[k] = o_r2[k] = o_r3[k] = 0;
         o_ht[k] = kInfH;
         if (n >= t.TN) continue;
         const uint32_t info = s_info[n];
-        const int wl = info_wl(info), yl = info_yl(info), j = info_j(info);
-        const int W = o.W0 + wl, y = o.y0 + yl;
-        pq[k] = info_p(info);
+        inf[k] = info;
+        tmask |= 1u << k;
+        const int W = o.W0 + info_wl(info), y = o.y0 + info_yl(info);
         if (W >= g.ng || y >= g.h) continue;
-        const int64_t i = ((int64_t)y * g.K + j) * g.P + W;
-        pi[k] = pq[k];
-        gi[k] = i;
+        vmask |= 1u << k;
+        const int64_t i = tile_g0 + (int64_t)info_yl(info) * g.SY +
+                          (int64_t)info_j(info) * g.P + info_wl(info);
         o_ex[k] = ld(&s.ex[i]);
         o_ht[k] = ld(&s.ht[i]);
         o_rc[k] = ld(&s.rc[i]);
@@ -815,18 +815,11 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     halo_commit(m, true, hr);
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
-        if (pq[k] < 0) continue;
-        const int p = pq[k];
-        if (pi[k] < 0) {
-            m.ht[p] = kInfH;
-            m.ex[p] = 0;
-            continue;
-        }
-        const int n = threadIdx.x + k * blockDim.x;
-        const uint32_t info = s_info[n];
-        s_exb[n] = (uint16_t)arc_exists(g, o.y0 + info_yl(info), info_j(info), o.W0 + info_wl(info));
+        if (!((tmask >> k) & 1u)) continue;
+        const int p = info_p(inf[k]);
         m.ex[p] = o_ex[k];
         m.ht[p] = o_ht[k];
+        if (!((vmask >> k) & 1u)) continue;
         m.rc[p] = o_rc[k];
         m.rr[p] = o_rr[k];
         m.rd[p] = o_rd[k];
@@ -844,49 +837,55 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     const int64_t gstride = s.rr - s.rc;         // global fields are equally spaced
     // Local iterations, one warp at a time and with no block barrier: each
     // warp compacts its own active nodes (positive excess, finite height; the
-    // nodes its lanes own) into a warp list with ballots, discharges the list
-    // 32 nodes at a time, and goes on to its next iteration.  Discharges of
-    // different warps run concurrently on shared memory; the lock-free argument
-    // that holds between tiles holds between warps (only a node's own warp
-    // lowers its excess, and residuals are consumed only by an arc's tail).
-    __shared__ uint16_t s_wlist[kTileThreads / 32][4 * 32 * 2];
-    const int64_t tile_g0 = (int64_t)o.y0 * g.SY + o.W0;
+    // nodes its lanes own) into a warp list of packed positions with ballots,
+    // discharges the list 32 nodes at a time, and goes on to its next
+    // iteration.  Discharges of different warps run concurrently on shared
+    // memory; the lock-free argument that holds between tiles holds between
+    // warps (only a node's own warp lowers its excess, and residuals are
+    // consumed only by an arc's tail).  Every load of a discharge depends only
+    // on the list entry, so they are in flight together.
+    __shared__ uint32_t s_wlist[kTileThreads / 32][8 * 32];
     unsigned nb_touch = 0;   // bit 0: left, 1: right, 2: up, 3: down neighbour tile received flow
     const int lane = threadIdx.x & 31;
-    uint16_t *wl_list = s_wlist[threadIdx.x >> 5];
+    uint32_t *wl_list = s_wlist[threadIdx.x >> 5];
     volatile int32_t *vex = m.ex;
     volatile int32_t *vht = m.ht;
     for (int it = 0; it < iters; it++) {
+        int32_t ce[NPT], ch[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; k++) {
+            const int p = info_p(inf[k]);
+            ce[k] = vex[p];
+            ch[k] = vht[p];
+        }
         int cnt = 0;
 #pragma unroll
         for (int k = 0; k < NPT; k++) {
-            const bool act = pi[k] >= 0 && vex[pi[k]] > 0 && vht[pi[k]] < kInfH;
+            const bool act = ((vmask >> k) & 1u) && ce[k] > 0 && ch[k] < kInfH;
             const unsigned bal = __ballot_sync(0xffffffffu, act);
-            if (act) wl_list[cnt + __popc(bal & ((1u << lane) - 1u))] =
-                (uint16_t)(threadIdx.x + k * blockDim.x);
+            if (act) wl_list[cnt + __popc(bal & ((1u << lane) - 1u))] = inf[k];
             cnt += __popc(bal);
         }
         __syncwarp();
         if (cnt == 0) continue;
         for (int li = lane; li < cnt; li += 32) {
-            const int n = wl_list[li];
-            const uint32_t info = s_info[n];
+            const uint32_t info = wl_list[li];
             const int p = info_p(info);
             const int wl = info_wl(info), yl = info_yl(info), j = info_j(info);
             const int64_t gin = tile_g0 + (int64_t)yl * g.SY + (int64_t)j * g.P + wl;
-            const unsigned exb = s_exb[n];
-            const int32_t e = vex[p];
-            const int32_t hu = vht[p];
-            if (e <= 0 || hu >= kInfH) continue;
-            int32_t rr[kSlots], hv[kSlots];
+            const unsigned exb = arc_exists(g, o.y0 + yl, j, o.W0 + wl);
             // all loads issued before any is used (the existing arcs' heights
             // are read whatever their residual), so they overlap
+            const int32_t e = vex[p];
+            const int32_t hu = vht[p];
+            int32_t rr[kSlots], hv[kSlots];
 #pragma unroll
             for (int q = 0; q < kSlots; q++) {
                 const bool ex = (exb >> q) & 1u;
                 rr[q] = ex ? smem_residual(m, t, g, p, q) : 0;
                 hv[q] = vht[p + (ex ? off[q] : 0)];
             }
+            if (e <= 0 || hu >= kInfH) continue;
             // residual and admissible slots as bit masks (registers only)
             unsigned resid = 0, adm = 0;
 #pragma unroll
@@ -897,15 +896,16 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
             }
             int32_t left = e;
             // push along the admissible slots, in slot order, until the
-            // excess is gone; the residual is re-read (it can only have grown)
+            // excess is gone; a slot's residual is the one loaded above (it
+            // can only have grown since: pushing it is always valid)
             for (unsigned bits = adm; bits && left > 0; bits &= bits - 1u) {
                 const int q = __ffs(bits) - 1;
+                int32_t r = 0;
+#pragma unroll
+                for (int qq = 0; qq < kSlots; qq++) r = qq == q ? rr[qq] : r;
+                const int32_t d = min(left, r);
                 const SlotTab st = s_slot[q];
                 int32_t *wp = sbase + p + st.a.x;
-                const int32_t w = *(volatile int32_t *)wp;
-                const int32_t r = st.a.z == 2 ? kInfR : st.a.z == 0 ? w : st.a.w - w;
-                const int32_t d = min(left, r);
-                if (d <= 0) continue;
                 red_add_smem(wp, st.a.z == 0 ? -d : d);
                 const int wl2 = wl + st.b.x, yl2 = yl + st.b.y;
                 if (wl2 < 0 || wl2 >= t.TW || yl2 < 0 || yl2 >= t.TH) {
@@ -938,9 +938,11 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     int still = 0;
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
-        if (pi[k] < 0) continue;
-        const int p = pi[k];
-        const int64_t i = gi[k];
+        if (!((vmask >> k) & 1u)) continue;
+        const uint32_t info = inf[k];
+        const int p = info_p(info);
+        const int64_t i = tile_g0 + (int64_t)info_yl(info) * g.SY +
+                          (int64_t)info_j(info) * g.P + info_wl(info);
         int32_t v;
         if ((v = m.ex[p] - o_ex[k])) atomicAdd(&s.ex[i], v);
         // the data-arc residual is the one word that can grow without a bound
