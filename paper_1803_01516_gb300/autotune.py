@@ -24,7 +24,8 @@ import torch
 from . import gazecut as gc
 from . import synth
 
-SCHEDULES = [(spr, li, rp) for spr in (8, 16, 32, 64) for li in (4, 8, 16) for rp in (4, 8, 16)]
+SCHEDULES = [(spr, li, rp, tf) for spr in (8, 16, 32, 64) for li in (4, 8, 16) for rp in (4, 8, 16)
+             for tf in (2, 4)]       # tf: tail iterations = tf x local iterations
 SHAPES = [(16, 8), (8, 8), (16, 4), (32, 4), (8, 4), (16, 2), (8, 2), (4, 4)]
 
 
@@ -77,9 +78,10 @@ def _save(d: dict):
 
 
 def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
-    spr, li, rp, tw, th = cfg
+    spr, li, rp, tw, th = cfg[:5]
+    ti = cfg[5] if len(cfg) > 5 else 0
     o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
-                     tile_h=th)
+                     tile_h=th, tail_iters=ti)
     try:
         gc.gs_tile_info(p, o)
     except RuntimeError:
@@ -105,7 +107,7 @@ def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
     return ts[len(ts) // 2]
 
 
-def tune(p: gc.Params, n_pairs: int = 1, save: bool = True) -> dict:
+def tune(p: gc.Params, n_pairs: int = 2, save: bool = True) -> dict:
     """Tile shape first (default schedule), then the schedule on the best shape,
     each measured on synthetic pairs of p's size."""
     wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
@@ -119,10 +121,10 @@ def tune(p: gc.Params, n_pairs: int = 1, save: bool = True) -> dict:
     for tw, th in SHAPES:
         results[f"16,8,8,{tw},{th}"] = _time_config(p, pairs, (16, 8, 8, tw, th))
     shape = [int(x) for x in min(results, key=results.get).split(",")][3:]
-    for spr, li, rp in SCHEDULES:
-        key = f"{spr},{li},{rp},{shape[0]},{shape[1]}"
+    for spr, li, rp, tf in SCHEDULES:
+        key = f"{spr},{li},{rp},{shape[0]},{shape[1]},{tf * li}"
         if key not in results:
-            results[key] = _time_config(p, pairs, (spr, li, rp, *shape))
+            results[key] = _time_config(p, pairs, (spr, li, rp, *shape, tf * li))
     best = min(results, key=results.get)
     entry = {"best": [int(x) for x in best.split(",")], "ms": results[best], "all_ms": results}
     if save:
@@ -167,8 +169,17 @@ def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpt
 
 if __name__ == "__main__":
     import sys
-    # tune the buckets given as w,h,D triples (default: the benchmark's sizes)
-    sizes = [tuple(int(x) for x in a.split(",")) for a in sys.argv[1:]] or [(384, 288, 16)]
+    # tune the buckets given as w,h,D triples (default: the benchmark's size),
+    # or, with --defaults, a size for every bucket of tuned_defaults.json
+    if sys.argv[1:] == ["--defaults"]:
+        sizes = []
+        for k in sorted(_defaults()):
+            d, n = (int(x[1:]) for x in k.split("-"))
+            h = 240
+            ng = max(8, round(2 ** n / (h * (d - 1))))
+            sizes.append((ng + 2 * (d - 1), h, d))
+    else:
+        sizes = [tuple(int(x) for x in a.split(",")) for a in sys.argv[1:]] or [(384, 288, 16)]
     for w, h, D in sizes:
         p = gc.Params(w=w, h=h, D=D, tau=30, lam=10)
         e = tune(p)
