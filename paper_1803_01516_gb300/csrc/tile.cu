@@ -306,7 +306,7 @@ __device__ __forceinline__ void halo_load(const SolveArgs &a, const int32_t *hsr
                                           int64_t gi, bool in, int kind, int32_t &h, int32_t &r1,
                                           int32_t &r2) {
     const State &s = a.s;
-    h = in ? ld(&hsrc[gi]) : kInfH;
+    h = (in && hsrc) ? ld(&hsrc[gi]) : kInfH;   // hsrc NULL: heights unknown (infinite)
     r1 = r2 = 0;
     if (with_res && in) {
         if (kind == 0) {
@@ -475,8 +475,9 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
     const State &s = a.s;
     const TileOrigin o = tile_origin(t, tile);
     const int dir = eff_dir(a);
+    // halo heights are not known yet in this pass: staged as infinite
     HaloRegs hr;
-    halo_issue(a, o, true, a.hgt, hr);
+    halo_issue(a, o, true, nullptr, hr);
     int pi[NPT], pq[NPT];
     unsigned mk[NPT];
     int64_t gi[NPT];
@@ -532,7 +533,7 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
             m.ht[p] = e > 0 ? 0 : kInfH;
         }
     }
-    halo_rest(a, m, o, true, a.hgt);
+    halo_rest(a, m, o, true, nullptr);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NPT; k++) {
@@ -557,17 +558,6 @@ __device__ long long relabel_init_tile(const SolveArgs &a, const TileSmem &m, in
             if (res) mk[k] |= 1u << q;
         }
         __stcg(&a.amask[gi[k]], (uint16_t)mk[k]);
-    }
-    // halo heights are not known yet in this pass: treat as infinite
-    for (int n = threadIdx.x; n < 2 * t.TH * g.K; n += blockDim.x) {
-        const int side = n / (t.TH * g.K), r = n - side * t.TH * g.K;
-        const int yl = r / g.K, j = r - yl * g.K;
-        m.ht[pidx(t, yl, j, side ? t.TW : -1)] = kInfH;
-    }
-    for (int n = threadIdx.x; n < 2 * g.K * t.TW; n += blockDim.x) {
-        const int side = n / (g.K * t.TW), r = n - side * g.K * t.TW;
-        const int j = r / t.TW, wl = r - j * t.TW;
-        m.ht[pidx(t, side ? t.TH : -1, j, wl)] = kInfH;
     }
     __syncthreads();
     // the first pass's relaxation is capped: the pass after it visits every
@@ -611,6 +601,7 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const TileOrigin o = tile_origin(t, tile);
+    const long long before = ld(&a.tile_cnt[tile]);   // issued now, used at the end
     HaloRegs hr;
     halo_issue(a, o, false, a.hgt, hr);
     int pi[NPT], pq[NPT];
@@ -669,7 +660,6 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
         if (nb >= 0) enqueue(dirty_next, list_next, count_next, nb);
     }
     if (ch) changed = 1;
-    const long long before = ld(&a.tile_cnt[tile]);
     __syncthreads();
     if (threadIdx.x == 0) __stcg(&a.tile_cnt[tile], (int32_t)tot);
     return tot - before;
