@@ -1004,9 +1004,9 @@ struct PairState {
     unsigned long long t_step;         // start of the current step (global timer)
 };
 
-// Per-pair control words of a launch.  claim packs the current step (16 bits,
-// for the queue slots), its number of items and the next item (24 bits each):
-// one atomic add both claims an item and tells which step it belongs to.
+// Per-pair control words of a launch.  claim packs the current step's queue
+// slot (step mod 3), its number of items and the next item (24 bits each):
+// one atomic add both claims an item and tells where its step's queue is.
 struct PairCtl {
     unsigned long long claim;
     unsigned int done;      // items of the current step completed
@@ -1032,7 +1032,9 @@ __device__ __forceinline__ void load_state(PairState *dst, const PairState *src)
 
 __device__ __forceinline__ unsigned long long pack_claim(unsigned step, unsigned items,
                                                          unsigned next) {
-    return ((unsigned long long)(step & 0xffffu) << 48) |
+    // bits 48-63: the step's queue slot (step mod 3), so a block that claims
+    // an item knows where the step's queue is from the claim alone
+    return ((unsigned long long)(step % 3u) << 48) |
            ((unsigned long long)(items & kItemMask) << 24) | (next & kItemMask);
 }
 
@@ -1231,13 +1233,17 @@ __device__ void pair_results(const BatchArgs &B, const PairState &st, const Solv
 // End of a pair's step (one thread, after every item completed): advance the
 // state machine -- through any steps that have no items -- and publish the
 // next step's claim word, or count the pair finished.
-__device__ void end_step(const BatchArgs &B, int p) {
+__device__ void end_step(const BatchArgs &B, int p, int slot) {
     PairCtl *c = B.ctl + p;
     const SolveArgs &a = B.pair[p];
     __threadfence();
+    // the step's sums, its number and the pair's state, loaded together
+    long long v0[4];
+    for (int k = 0; k < 4; k++) v0[k] = *(volatile long long *)&c->red[slot][k];
+    unsigned step = *(volatile unsigned *)&c->step;
     PairState st;
     load_state(&st, &c->st);
-    unsigned step = *(volatile unsigned *)&c->step;
+    bool first = true;
     unsigned items = 0;
     const unsigned long long t_now = now_ns();
     if (st.phase == PH_SWEEP) st.ns_sweep += (long long)(t_now - st.t_step);
@@ -1245,7 +1251,11 @@ __device__ void end_step(const BatchArgs &B, int p) {
     st.t_step = t_now;
     for (;;) {
         long long v[4];
-        for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&c->red[step % 3][k];
+        if (first && step % 3 == (unsigned)slot)
+            for (int k = 0; k < 4; k++) v[k] = v0[k];
+        else
+            for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&c->red[step % 3][k];
+        first = false;
         advance(st, a, v, B.extract);
         const unsigned next = step + 1;
         for (int k = 0; k < 4; k++) c->red[next % 3][k] = 0;
@@ -1266,7 +1276,9 @@ __device__ void end_step(const BatchArgs &B, int p) {
 template <int NPT>
 __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant__ BatchArgs B) {
     extern __shared__ int32_t smem[];
-    __shared__ int s_claim[4];     // pair, item, step (low 32 bits), exit flag
+    // pair, item, queue slot of the step, exit flag, items of the step, the
+    // queued tile at the item (speculative), the item's tile count (speculative)
+    __shared__ int s_claim[7];
     __shared__ PairState s_st;
     int tables_for = -1;           // pair whose tile-shape tables the block holds
     // block 0 starts every pair and publishes its first step
@@ -1320,11 +1332,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
                     const unsigned idx = (unsigned)(w & kItemMask);
                     if (idx >= items) continue;
                     __threadfence();
+                    // everything the item needs, loaded together: the pair's
+                    // state, and both ways the item may name its tile (the
+                    // queued tile at this slot, or tile idx with its count)
+                    const int sl = (int)((w >> 48) & 3u);
+                    const SolveArgs &ap = B.pair[p];
+                    const int32_t qt = ld(&ap.tile_list[sl * ap.t.T + idx]);
+                    const int32_t tc = ld(&ap.tile_cnt[idx]);
+                    load_state(&s_st, &c->st);
                     s_claim[0] = p;
                     s_claim[1] = (int)idx;
-                    s_claim[2] = (int)*(volatile unsigned *)&c->step;
+                    s_claim[2] = sl;
                     s_claim[3] = 0;
-                    load_state(&s_st, &c->st);
+                    s_claim[4] = (int)items;
+                    s_claim[5] = qt;
+                    s_claim[6] = tc;
                     got = 1;
                 }
                 if (!got) {
@@ -1340,8 +1362,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
         __syncthreads();
         if (s_claim[3]) break;
         const int pr = s_claim[0];
-        const unsigned step = (unsigned)s_claim[2];
-        const int slot = (int)(step % 3), next = (int)((step + 1) % 3);
+        const int slot = s_claim[2], next = (slot + 1) % 3;
         PairCtl *c = B.ctl + pr;
         const SolveArgs &a = B.pair[pr];
         if (pr != tables_for) {      // uniform: every thread read the same claim
@@ -1354,15 +1375,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
         const TileSmem m = tile_smem(smem, a.t.PN);
         int32_t *list_next = a.tile_list + next * T;
         int32_t *count_next = &c->qcount[next];
-        __shared__ int s_tile;
-        if (threadIdx.x == 0) {
-            int tile = s_claim[1];
-            if (queued(s_st)) tile = ld(&a.tile_list[slot * T + tile]);
-            else if (phase == PH_SWEEP && ld(&a.tile_cnt[tile]) <= 0) tile = -1;   // nothing to sweep
-            s_tile = tile;
-        }
-        __syncthreads();
-        const int tile = s_tile;
+        const int tile = queued(s_st) ? s_claim[5]
+                         : (phase == PH_SWEEP && s_claim[6] <= 0) ? -1   // nothing to sweep
+                                                                   : s_claim[1];
         long long va = 0, vb = 0, vc = 0;
         int ovf = 0;
         if (tile >= 0) {
@@ -1405,11 +1420,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
             if (vc) atomicAdd((unsigned long long *)&rp[2], (unsigned long long)vc);
             if (ovf) atomicAdd((unsigned long long *)&rp[3], 1ull);
             __threadfence();
-            // the step cannot end before this item does, so the claim word
-            // still holds this step's item count
-            const unsigned total = (unsigned)((*(volatile unsigned long long *)&c->claim >> 24) &
-                                              kItemMask);
-            if (atomicAdd(&c->done, 1u) + 1u == total) end_step(B, pr);
+            // the step's item count, as claimed (the step cannot end before
+            // this item does)
+            const unsigned total = (unsigned)s_claim[4];
+            if (atomicAdd(&c->done, 1u) + 1u == total) end_step(B, pr, slot);
         }
         __syncthreads();
     }
