@@ -112,12 +112,17 @@ typedef struct gs_solve_opts {
                                     running end with GS_ERR_TIMEOUT (state valid,
                                     resumable); 0: 60 s.  In a batch the smallest
                                     non-zero value among the descriptors applies. */
+    int32_t cta_threads;         /* TILED: threads per block of the persistent launch,
+                                    0 or 512 (one block per SM) or 256 (two blocks per
+                                    SM when two tiles fit its shared memory, each
+                                    tile on half the threads).  A batch runs 256 only
+                                    when every descriptor asks for it. */
 } gs_solve_opts;
 
 /* Host-side check of solve options (the same checks gs_maxflow_solve and
  * gs_solve_batched apply): GS_OK or GS_ERR_INVAL (unknown mode or engine,
  * sweeps_per_relabel < 1, max_iters < 1, a negative count, fixed_sweeps < 0 in
- * GS_MODE_FIXED_SWEEPS, idle_limit_us < 0). */
+ * GS_MODE_FIXED_SWEEPS, idle_limit_us < 0, cta_threads not 0, 256 or 512). */
 GS_API int gs_check_solve_opts(const gs_solve_opts *o);
 
 /* Derived sizes (0 when the params are invalid). */

@@ -27,6 +27,7 @@ from . import synth
 SCHEDULES = [(spr, li, rp, tf) for spr in (8, 16, 32, 64) for li in (4, 8, 16) for rp in (4, 8, 16)
              for tf in (2, 4)]       # tf: tail iterations = tf x local iterations
 SHAPES = [(16, 8), (8, 8), (16, 4), (32, 4), (8, 4), (16, 2), (8, 2), (4, 4)]
+CTA_THREADS = (512, 256)     # one block per SM, or two half-size blocks
 
 
 def cache_path() -> str:
@@ -80,8 +81,9 @@ def _save(d: dict):
 def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
     spr, li, rp, tw, th = cfg[:5]
     ti = cfg[5] if len(cfg) > 5 else 0
+    bt = cfg[6] if len(cfg) > 6 else 0
     o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
-                     tile_h=th, tail_iters=ti)
+                     tile_h=th, tail_iters=ti, cta_threads=bt)
     try:
         gc.gs_tile_info(p, o)
     except RuntimeError:
@@ -108,8 +110,10 @@ def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
 
 
 def tune(p: gc.Params, n_pairs: int = 2, save: bool = True) -> dict:
-    """Tile shape first (default schedule), then the schedule on the best shape,
-    each measured on synthetic pairs of p's size."""
+    """Tile shape and block size first (default schedule), then the schedule on
+    the best of those, each measured on synthetic pairs of p's size.  An entry
+    is [sweeps_per_relabel, local_iters, relabel_passes, tile_w, tile_h,
+    tail_iters, cta_threads]."""
     wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
                         scene="layers", n_layers=5, n_slanted=2,
                         max_disp=min(2 * (p.D - 1), 40), seed_base=77)
@@ -119,12 +123,14 @@ def tune(p: gc.Params, n_pairs: int = 2, save: bool = True) -> dict:
         pairs.append((torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()))
     results = {}
     for tw, th in SHAPES:
-        results[f"16,8,8,{tw},{th}"] = _time_config(p, pairs, (16, 8, 8, tw, th))
-    shape = [int(x) for x in min(results, key=results.get).split(",")][3:]
+        for bt in CTA_THREADS:
+            results[f"16,8,8,{tw},{th},0,{bt}"] = _time_config(p, pairs, (16, 8, 8, tw, th, 0, bt))
+    first = [int(x) for x in min(results, key=results.get).split(",")]
+    tw, th, bt = first[3], first[4], first[6]
     for spr, li, rp, tf in SCHEDULES:
-        key = f"{spr},{li},{rp},{shape[0]},{shape[1]},{tf * li}"
+        key = f"{spr},{li},{rp},{tw},{th},{tf * li},{bt}"
         if key not in results:
-            results[key] = _time_config(p, pairs, (spr, li, rp, *shape, tf * li))
+            results[key] = _time_config(p, pairs, (spr, li, rp, tw, th, tf * li, bt))
     best = min(results, key=results.get)
     entry = {"best": [int(x) for x in best.split(",")], "ms": results[best], "all_ms": results}
     if save:
@@ -156,8 +162,9 @@ def tuned_opts(p: gc.Params, tune_if_missing: bool = False, **kw) -> gc.SolveOpt
     spr, li, rp = best[:3]
     tw, th = (best[3], best[4]) if len(best) >= 5 else (0, 0)
     ti = best[5] if len(best) >= 6 else 0          # tail iterations (0: library default)
+    bt = best[6] if len(best) >= 7 else 0          # threads per block (0: library default)
     o = gc.SolveOpts(sweeps_per_relabel=spr, local_iters=li, relabel_passes=rp, tile_w=tw,
-                     tile_h=th, tail_iters=ti, **kw)
+                     tile_h=th, tail_iters=ti, cta_threads=bt, **kw)
     try:
         gc.gs_tile_info(p, o)
     except RuntimeError:

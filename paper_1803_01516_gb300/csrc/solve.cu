@@ -162,6 +162,7 @@ extern "C" int gs_check_solve_opts(const gs_solve_opts *o) {
         return GS_ERR_INVAL;
     if (o->mode != GS_MODE_EXACT && o->mode != GS_MODE_FIXED_SWEEPS) return GS_ERR_INVAL;
     if (o->mode == GS_MODE_FIXED_SWEEPS && o->fixed_sweeps < 0) return GS_ERR_INVAL;
+    if (o->cta_threads != 0 && o->cta_threads != 256 && o->cta_threads != 512) return GS_ERR_INVAL;
     return GS_OK;
 }
 

@@ -31,7 +31,7 @@
 
 namespace gs {
 
-constexpr int kTileThreads = 512;
+constexpr int kTileThreads = 512;            // threads per block (256 on request: two per SM)
 constexpr int kInitOuter = 2;                 // relaxation rounds of a first relabel pass
 constexpr int kMaxTileNodes = 4096;           // own nodes per tile (8 per thread at most)
 
@@ -754,7 +754,7 @@ __device__ void build_tables(const SolveArgs &a) {
 
 
 // Up to local_iters push/relabel iterations of one tile in shared memory.
-template <int NPT>
+template <int NPT, int BT>
 __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round, int iters,
                            int &overflow, int32_t *list_next, int32_t *count_next) {
     const Geom &g = a.g;
@@ -834,7 +834,7 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     // warps (only a node's own warp lowers its excess, and residuals are
     // consumed only by an arc's tail).  Every load of a discharge depends only
     // on the list entry, so they are in flight together.
-    __shared__ uint32_t s_wlist[kTileThreads / 32][8 * 32];
+    __shared__ uint32_t s_wlist[BT / 32][8 * 32];
     unsigned nb_touch = 0;   // bit 0: left, 1: right, 2: up, 3: down neighbour tile received flow
     const int lane = threadIdx.x & 31;
     uint32_t *wl_list = s_wlist[threadIdx.x >> 5];
@@ -1273,8 +1273,8 @@ __device__ void end_step(const BatchArgs &B, int p, int slot) {
     if (st.phase == PH_DONE) atomicAdd(&B.bar->active, 1);
 }
 
-template <int NPT>
-__global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant__ BatchArgs B) {
+template <int NPT, int BT>
+__global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_constant__ BatchArgs B) {
     extern __shared__ int32_t smem[];
     // pair, item, queue slot of the step, exit flag, items of the step, the
     // queued tile at the item (speculative), the item's tile count (speculative)
@@ -1402,7 +1402,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
             } else if (phase == PH_SWEEP) {
                 const int cur = (int)(s_st.round & 1);
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
-                sweep_tile<NPT>(a, m, tile, cur, s_st.tail ? a.tail_iters : a.local_iters, ovf,
+                sweep_tile<NPT, BT>(a, m, tile, cur, s_st.tail ? a.tail_iters : a.local_iters, ovf,
                                 list_next, count_next);
                 ovf = __syncthreads_or(ovf);
                 va = 1;
@@ -1445,10 +1445,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(const __grid_constant
 // nodes per thread (4 preferred).  Wider tiles first (coalesced rows of 32
 // sites), then the tallest that fits up to TH = 4.
 static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int want_w = 0,
-                      int want_h = 0) {
-    // dynamic shared memory of a tile; with the kernel's ~42 KB of static
-    // shared arrays it must stay under the 227 KB a block may opt in to
-    const size_t budget = 180 * 1024;
+                      int want_h = 0, int bt = kTileThreads) {
+    // dynamic shared memory of a tile; with the kernel's ~34 KB of static
+    // shared arrays it must stay under the 227 KB a block may opt in to.  With
+    // 256-thread blocks the library's own choice first tries to keep two tiles
+    // within an SM (long chains fall back to one block per SM).
+    const size_t budgets[2] = {(bt == 256 && !want_w) ? 80 * 1024 : 180 * 1024, 180 * 1024};
     // more sites first, squarer first among equals: a breadth-first path then
     // crosses fewer tile borders (measured: 8x8 beats 16x4 at 31 depth layers,
     // 8x4 beats 16x2 at 47)
@@ -1460,8 +1462,9 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
             want_h > 8)
             return false;
     }
-    for (int pass = 0; pass < 2; pass++) {
-        const int max_nodes = (pass == 0 ? 4 : 8) * kTileThreads;
+    for (int pass = 0; pass < 4; pass++) {
+        const size_t budget = budgets[pass / 2];
+        const int max_nodes = (pass % 2 == 0 ? 4 : 8) * bt;
         for (int ci = 0; ci < (want_w ? 1 : (int)(sizeof(cand) / sizeof(cand[0]))); ci++) {
             const int TW = want_w ? want_w : cand[ci][0], TH = want_w ? want_h : cand[ci][1];
             const int TN = TH * g.K * TW;
@@ -1511,7 +1514,7 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
             t.tiles_w = (g.ng + TW - 1) / TW;
             t.tiles_h = (g.h + TH - 1) / TH;
             t.T = t.tiles_w * t.tiles_h;
-            npt = pass == 0 ? 4 : 8;
+            npt = pass % 2 == 0 ? 4 : 8;
             smem = bytes;
             return true;
         }
@@ -1529,11 +1532,11 @@ size_t tiled_work_extra(const Geom &g) {
 
 // Per-pair arguments from the pair's geometry, state and workspace.
 static int setup_args(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
-                      SolveArgs &a, int &npt, size_t &smem) {
+                      SolveArgs &a, int &npt, size_t &smem, int bt) {
     memset(&a, 0, sizeof(a));
     a.g = g;
     a.s = s;
-    if (!pick_tile(g, a.t, npt, smem, o->tile_w, o->tile_h)) return GS_ERR_INVAL;
+    if (!pick_tile(g, a.t, npt, smem, o->tile_w, o->tile_h, bt)) return GS_ERR_INVAL;
     // a step's item count travels in 24 bits of the claim word
     if (a.t.T > (int)(kItemMask - 4096)) return GS_ERR_INVAL;
     char *extra = (char *)w.mark + round_up(g.N * sizeof(int32_t), 256);
@@ -1561,9 +1564,10 @@ static void solve_fields(SolveArgs &a, const gs_solve_opts *o) {
 // Cooperative launch of the batch kernel with the whole grid resident.  The
 // launch goes through cudaLaunchKernelEx with the cooperative attribute, so a
 // caller may capture it in a CUDA graph.
-static int launch_batch(const BatchArgs &B, int npt, size_t smem, int total_tiles,
+static int launch_batch(const BatchArgs &B, int npt, size_t smem, int total_tiles, int bt,
                         cudaStream_t st) {
-    void (*kern)(const BatchArgs) = npt == 4 ? k_batch<4> : k_batch<8>;
+    void (*kern)(const BatchArgs) = bt == 256 ? (npt == 4 ? k_batch<4, 256> : k_batch<8, 256>)
+                                              : (npt == 4 ? k_batch<4, 512> : k_batch<8, 512>);
     int dev = 0;
     GS_CUDA_TRY(cudaGetDevice(&dev));
     int sms = 0, coop = 0;
@@ -1572,11 +1576,11 @@ static int launch_batch(const BatchArgs &B, int npt, size_t smem, int total_tile
     if (!coop) return GS_ERR_CUDA;
     GS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem));
+    GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bt, smem));
     if (per_sm < 1) return GS_ERR_INVAL;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(std::min(per_sm * sms, total_tiles));
-    cfg.blockDim = dim3(kTileThreads);
+    cfg.blockDim = dim3(bt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1601,16 +1605,20 @@ static unsigned long long idle_limit_ns(const gs_solve_opts *o) {
                                 : kDefaultIdleLimitNs;
 }
 
-static int run_batch(BatchArgs &B, int npt, size_t smem, void *ctrl_mem, cudaStream_t st) {
+static int run_batch(BatchArgs &B, int npt, size_t smem, int bt, void *ctrl_mem,
+                     cudaStream_t st) {
     B.bar = (Ctrl *)ctrl_mem;
     B.ctl = (PairCtl *)((char *)ctrl_mem + 256);
     int total = 0;
     for (int p = 0; p < B.n; p++) total += B.pair[p].t.T;
     GS_CUDA_TRY(cudaMemsetAsync(ctrl_mem, 0, 256 + (size_t)B.n * sizeof(PairCtl), st));
-    return launch_batch(B, npt, smem, total, st);
+    return launch_batch(B, npt, smem, total, bt, st);
 }
 
 size_t batch_ctrl_bytes() { return kBatchCtrlBytes; }
+
+// Threads per block a pair's options ask for.
+static int cta_threads(const gs_solve_opts *o) { return o->cta_threads == 256 ? 256 : 512; }
 
 int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
                 int32_t *status, cudaStream_t st) {
@@ -1623,12 +1631,13 @@ int tiled_solve(const Geom &g, const State &s, const Work &w, const gs_solve_opt
     B.idle_limit_ns = idle_limit_ns(o);
     int npt;
     size_t smem;
-    int rc = setup_args(g, s, w, o, B.pair[0], npt, smem);
+    const int bt = cta_threads(o);
+    int rc = setup_args(g, s, w, o, B.pair[0], npt, smem, bt);
     if (rc) return rc;
     solve_fields(B.pair[0], o);
     B.pair[0].status = status;
     GS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
-    return run_batch(B, npt, smem, (char *)w.ctrl + 256, st);
+    return run_batch(B, npt, smem, bt, (char *)w.ctrl + 256, st);
 }
 
 int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_opts *o,
@@ -1642,7 +1651,8 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
     B.idle_limit_ns = idle_limit_ns(o);
     int npt;
     size_t smem;
-    int rc = setup_args(g, s, w, o, B.pair[0], npt, smem);
+    const int bt = cta_threads(o);
+    int rc = setup_args(g, s, w, o, B.pair[0], npt, smem, bt);
     if (rc) return rc;
     SolveArgs &a = B.pair[0];
     a.hgt = w.mark;
@@ -1652,7 +1662,7 @@ int tiled_extract(const Geom &g, const State &s, const Work &w, const gs_solve_o
     a.labels = labels;
     a.flow = flow;
     a.status = status;
-    return run_batch(B, npt, smem, (char *)w.ctrl + 256, st);
+    return run_batch(B, npt, smem, bt, (char *)w.ctrl + 256, st);
 }
 
 }  // namespace gs
@@ -1663,7 +1673,8 @@ extern "C" int gs_tile_info(const gs_params *p, const gs_solve_opts *o, int32_t 
     gs::TileGeom t;
     int npt;
     size_t smem;
-    if (!gs::pick_tile(g, t, npt, smem, o->tile_w, o->tile_h)) return GS_ERR_INVAL;
+    if (!gs::pick_tile(g, t, npt, smem, o->tile_w, o->tile_h, gs::cta_threads(o)))
+        return GS_ERR_INVAL;
     out[0] = t.TW;
     out[1] = t.TH;
     out[2] = t.T;
@@ -1694,6 +1705,10 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
     B.idle_limit_ns = kDefaultIdleLimitNs;
     int npt_max = 4;
     size_t smem_max = 0;
+    // one block size for the launch: 256 threads only when every pair asks
+    int bt = 256;
+    for (int i = 0; i < n; i++)
+        if (cta_threads(&descs[i].o) != 256) bt = 512;
     for (int i = 0; i < n; i++) {
         const gs_pair_desc &d = descs[i];
         Geom g;
@@ -1708,7 +1723,7 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
         const Work w = work_view(d.workspace, g);
         int npt;
         size_t smem;
-        if (setup_args(g, s, w, &d.o, B.pair[i], npt, smem) != GS_OK) return GS_ERR_INVAL;
+        if (setup_args(g, s, w, &d.o, B.pair[i], npt, smem, bt) != GS_OK) return GS_ERR_INVAL;
         solve_fields(B.pair[i], &d.o);
         B.pair[i].status = d.status;
         E.pair[i] = B.pair[i];
@@ -1733,7 +1748,7 @@ extern "C" int gs_solve_batched(const gs_pair_desc *descs, int32_t n, void *batc
         GS_CUDA_TRY(cudaMemsetAsync(B.pair[i].ctrl, 0, sizeof(Ctrl), st));
     }
     E.idle_limit_ns = B.idle_limit_ns;
-    int rc = run_batch(B, npt_max, smem_max, batch_ws, st);
+    int rc = run_batch(B, npt_max, smem_max, bt, batch_ws, st);
     if (rc) return rc;
-    return run_batch(E, npt_max, smem_max, batch_ws, st);
+    return run_batch(E, npt_max, smem_max, bt, batch_ws, st);
 }

@@ -52,7 +52,7 @@ class GsSolveOpts(ctypes.Structure):
                 ("max_iters", ctypes.c_int64), ("local_iters", ctypes.c_int32),
                 ("relabel_passes", ctypes.c_int32), ("tail_iters", ctypes.c_int32),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("idle_limit_us", ctypes.c_int32)]
+                ("idle_limit_us", ctypes.c_int32), ("cta_threads", ctypes.c_int32)]
 
 
 class GsPairDesc(ctypes.Structure):
@@ -100,11 +100,13 @@ class SolveOpts:
     tile_w: int = 0               # 0: library default
     tile_h: int = 0
     idle_limit_us: int = 0        # 0: library default (60 s)
+    cta_threads: int = 0          # 0: 512 (one block per SM); 256: two blocks per SM
 
     def c(self) -> GsSolveOpts:
         return GsSolveOpts(self.mode, self.sweeps_per_relabel, self.fixed_sweeps, self.engine,
                            self.max_iters, self.local_iters, self.relabel_passes,
-                           self.tail_iters, self.tile_w, self.tile_h, self.idle_limit_us)
+                           self.tail_iters, self.tile_w, self.tile_h, self.idle_limit_us,
+                           self.cta_threads)
 
 
 _lib = None

@@ -152,7 +152,7 @@ def test_params_and_options_pack_like_the_header(lib):
     import ctypes
     from paper_1803_01516_gb300 import gazecut as gc
     assert ctypes.sizeof(gc.GsParams) == 9 * 4
-    assert ctypes.sizeof(gc.GsSolveOpts) == 48
+    assert ctypes.sizeof(gc.GsSolveOpts) == 56      # 12 int32 + one int64, 8-byte aligned
     p = gc.Params(w=100, h=10, D=8, tau=5, lam=3)
     c = p.c()
     assert (c.dis0, c.direction, c.inhibit, c.vertical_inhibit) == (14, 0, 1023, 1)
@@ -171,6 +171,7 @@ def test_solve_options_checked_alike_for_single_and_batched_solves(lib):
     bad = [gc.SolveOpts(mode=7), gc.SolveOpts(engine=3), gc.SolveOpts(sweeps_per_relabel=0),
            gc.SolveOpts(max_iters=0), gc.SolveOpts(local_iters=-1), gc.SolveOpts(relabel_passes=-2),
            gc.SolveOpts(tail_iters=-1), gc.SolveOpts(idle_limit_us=-5),
+           gc.SolveOpts(cta_threads=384), gc.SolveOpts(cta_threads=128),
            gc.SolveOpts(mode=gc.GS_MODE_FIXED_SWEEPS, fixed_sweeps=-1)]
     p = gc.Params(w=64, h=8, D=4, tau=30, lam=2)
     fake = ctypes.c_void_p(256)

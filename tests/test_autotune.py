@@ -51,3 +51,20 @@ def test_unparseable_keys_are_ignored(tune):
     table = {"junk": {"best": [1, 1, 1]}, "D16-n20": {"best": [32, 4, 8, 16, 8]}}
     p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
     assert tune._nearest(table, p)["best"] == [32, 4, 8, 16, 8]
+
+
+def test_block_size_entry(tune):
+    """A seventh entry element sets the threads per block; the library's own
+    shape for 256-thread blocks keeps two tiles within an SM's shared memory."""
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
+    with open(tune.cache_path(), "w") as f:
+        json.dump({tune.bucket(p): {"best": [16, 8, 16, 8, 8, 16, 256], "ms": 1.0}}, f)
+    o = tune.tuned_opts(p)
+    assert o.cta_threads == 256 and (o.tile_w, o.tile_h, o.tail_iters) == (8, 8, 16)
+    info = gc.gs_tile_info(p, gc.SolveOpts(cta_threads=256))
+    assert (info["tile_w"], info["tile_h"]) == (8, 8)
+    assert 2 * (info["smem_bytes"] + 26 * 1024) <= 228 * 1024
+    # 512 threads (the default) take the larger tile
+    info = gc.gs_tile_info(p, gc.SolveOpts())
+    assert info["tile_w"] * info["tile_h"] > 64

@@ -200,3 +200,23 @@ def test_batch_workload_of_64_pairs_matches_oracle_pair_by_pair(gc):
             ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
             assert int(b.flow.item()) == ref["flow"], k
             assert np.array_equal(X, ref["labels"]), k
+
+
+@pytest.mark.parametrize("all256", [True, False])
+def test_batched_block_size(gc, all256):
+    """A batch runs on 256-thread blocks when every pair asks for them and on
+    512-thread blocks otherwise; either way each pair equals the oracle."""
+    pairs = _uneven_batch(6, 4)
+    params = [gc.Params(w=wl.w, h=wl.h, D=wl.D, tau=wl.tau, lam=wl.lam, inhibit=wl.inhibit,
+                        vertical_inhibit=vi) for wl, _, _, vi in pairs]
+    opts = [gc.SolveOpts(cta_threads=256 if (all256 or i % 2) else 0) for i in range(len(pairs))]
+    batch = gc.Batch(params, opts)
+    gc.gs_solve_batched(batch, [torch.from_numpy(L).cuda() for _, L, _, _ in pairs],
+                        [torch.from_numpy(R).cuda() for _, _, R, _ in pairs])
+    torch.cuda.synchronize()
+    for (wl, L, R, vi), b in zip(pairs, batch.bufs):
+        C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+        ref = oracle.solve(C, wl.lam, wl.inhibit, vi)
+        assert int(b.status.item()) == gc.GS_OK
+        assert int(b.flow.item()) == ref["flow"]
+        assert np.array_equal(b.labels.cpu().numpy(), ref["labels"])

@@ -319,3 +319,43 @@ def test_chain_prepass_changes_time_not_the_cut(gc, engine, which):
         assert int(buf.status.item()) == gc.GS_OK
         assert int(buf.flow.item()) == ref["flow"]
         assert np.array_equal(buf.labels.cpu().numpy(), ref["labels"])
+
+
+@pytest.mark.parametrize("shape,lam,inh,vi,hi,tile", [
+    ((37, 45, 5), 3, 50, 1, 20, (0, 0)),
+    ((19, 70, 9), 2, 1023, 0, 30, (8, 8)),
+    ((7, 45, 64), 3, 1023, 1, 30, (0, 0)),
+    ((2, 9, 200), 2, 1023, 1, 40, (0, 0)),
+    ((11, 97, 16), 10, 1023, 1, 30, (16, 8)),
+    ((21, 64, 7), 1, 3, 1, 40, (4, 4)),
+])
+@pytest.mark.parametrize("direction", [1, 2])
+def test_two_blocks_per_sm_exact(gc, shape, lam, inh, vi, hi, tile, direction):
+    """256-thread blocks (two per SM where two tiles fit): the library's shape
+    and explicit ones give the canonical cut in both solve directions."""
+    rng = np.random.default_rng(sum(shape) * 11 + lam)
+    C = rng.integers(0, hi + 1, size=shape).astype(np.int32)
+    o = gc.SolveOpts(cta_threads=256, tile_w=tile[0], tile_h=tile[1])
+    X, flow, status, _ = _solve_costs(gc, C, lam, inh, vi, o, direction)
+    ref = oracle.solve(C, lam, inh, vi)
+    assert status == gc.GS_OK
+    assert flow == ref["flow"]
+    assert np.array_equal(X, ref["labels"])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_two_blocks_per_sm_main_pair(gc, seed):
+    """384x288 pairs with 16 depth numbers on 256-thread blocks (8x8 tiles, two
+    blocks per SM), with the autotuned schedule, equal the oracle."""
+    wl = synth.MAIN
+    L, R, _ = synth.make_pair(wl, seed)
+    p = _params(gc, wl)
+    o = gc.SolveOpts(cta_threads=256, tile_w=8, tile_h=8, tail_iters=16, relabel_passes=16)
+    assert gc.gs_tile_info(p, o)["smem_bytes"] < 80 * 1024
+    labels, flow, status = gc.solve_pair(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda(), p, o)
+    torch.cuda.synchronize()
+    C = oracle.cost_volume(L, R, wl.D, 2 * (wl.D - 1), wl.tau)
+    ref = oracle.solve(C, wl.lam, wl.inhibit, 1)
+    assert int(status.item()) == gc.GS_OK
+    assert int(flow.item()) == ref["flow"]
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
