@@ -428,7 +428,7 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
     // arc reads the node's own height and is masked out), so they overlap:
     // a height read stale inside a round only delays convergence, and the
     // round that ends the loop changed nothing after fresh reads.
-    constexpr int kInner = 4;
+    constexpr int kInner = 2;
     int32_t *ht = m.ht;
     bool any_change = false;
     for (int outer = 0;; outer++) {
@@ -756,7 +756,8 @@ __device__ void build_tables(const SolveArgs &a) {
 // Up to local_iters push/relabel iterations of one tile in shared memory.
 template <int NPT, int BT>
 __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round, int iters,
-                           int &overflow, int32_t *list_next, int32_t *count_next) {
+                           int &overflow, int32_t *list_next, int32_t *count_next,
+                           const unsigned *done_ctr, unsigned items) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const State &s = a.s;
@@ -764,7 +765,11 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     int32_t *act_next = a.tile_act + ((round + 1) & 1) * t.T;
     const int64_t tile_g0 = (int64_t)o.y0 * g.SY + o.W0;
     __shared__ unsigned s_touch;
-    if (threadIdx.x == 0) s_touch = 0;   // read only after the staging barrier below
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) {
+        s_touch = 0;   // read only after the staging barrier below
+        s_stop = 0;
+    }
     HaloRegs hr;
     halo_issue(a, o, true, s.ht, hr);
     // own node k of this thread: its packed position (s_info) and whether it
@@ -840,7 +845,20 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     uint32_t *wl_list = s_wlist[threadIdx.x >> 5];
     volatile int32_t *vex = m.ex;
     volatile int32_t *vht = m.ht;
+    // Straggler cut: a step ends when its last item does, so a visit still
+    // running when nearly all of its step's items are done (all but 1 +
+    // items / 8) stops after half its local iterations.  Its tile keeps its
+    // work and is queued for the next round.  Thread 0 reads the step's done
+    // count once per iteration and uses it one iteration later (the load's
+    // latency hides behind the iteration).
+    unsigned seen = 0;
+    const unsigned margin = 1 + items / 8;
     for (int it = 0; it < iters; it++) {
+        if (threadIdx.x == 0) {
+            if (it >= 2 && seen + margin >= items) s_stop = 1;
+            seen = *(volatile const unsigned *)done_ctr;
+        }
+        if (it >= iters / 2 && __shfl_sync(0xffffffffu, *(volatile int *)&s_stop, 0)) break;
         int32_t ce[NPT], ch[NPT];
 #pragma unroll
         for (int k = 0; k < NPT; k++) {
@@ -1237,9 +1255,11 @@ __device__ void end_step(const BatchArgs &B, int p, int slot) {
     PairCtl *c = B.ctl + p;
     const SolveArgs &a = B.pair[p];
     __threadfence();
-    // the step's sums, its number and the pair's state, loaded together
+    // the step's sums, its number, the pair's state and the queue the step
+    // filled for the next one, loaded together
     long long v0[4];
     for (int k = 0; k < 4; k++) v0[k] = *(volatile long long *)&c->red[slot][k];
+    const int32_t q0 = *(volatile int32_t *)&c->qcount[(slot + 1) % 3];
     unsigned step = *(volatile unsigned *)&c->step;
     PairState st;
     load_state(&st, &c->st);
@@ -1251,7 +1271,8 @@ __device__ void end_step(const BatchArgs &B, int p, int slot) {
     st.t_step = t_now;
     for (;;) {
         long long v[4];
-        if (first && step % 3 == (unsigned)slot)
+        const bool pre = first && step % 3 == (unsigned)slot;   // the prefetched words apply
+        if (pre)
             for (int k = 0; k < 4; k++) v[k] = v0[k];
         else
             for (int k = 0; k < 4; k++) v[k] = *(volatile long long *)&c->red[step % 3][k];
@@ -1260,7 +1281,9 @@ __device__ void end_step(const BatchArgs &B, int p, int slot) {
         const unsigned next = step + 1;
         for (int k = 0; k < 4; k++) c->red[next % 3][k] = 0;
         c->qcount[(next + 1) % 3] = 0;
-        items = step_items(st, a, c, next);
+        items = st.phase == PH_DONE ? 0u
+                : (pre && queued(st)) ? (unsigned)q0
+                                      : step_items(st, a, c, next);
         step = next;
         if (st.phase == PH_DONE || items > 0) break;
     }
@@ -1403,7 +1426,7 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
                 const int cur = (int)(s_st.round & 1);
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
                 sweep_tile<NPT, BT>(a, m, tile, cur, s_st.tail ? a.tail_iters : a.local_iters, ovf,
-                                list_next, count_next);
+                                list_next, count_next, &c->done, (unsigned)s_claim[4]);
                 ovf = __syncthreads_or(ovf);
                 va = 1;
             } else {   // PH_LABELS
@@ -1450,7 +1473,8 @@ static bool pick_tile(const Geom &g, TileGeom &t, int &npt, size_t &smem, int wa
     // shared arrays it must stay under the 227 KB a block may opt in to.  With
     // 256-thread blocks the library's own choice first tries to keep two tiles
     // within an SM (long chains fall back to one block per SM).
-    const size_t budgets[2] = {(bt == 256 && !want_w) ? 80 * 1024 : 180 * 1024, 180 * 1024};
+    const size_t budgets[2] = {(bt == 256 && !want_w) ? size_t(80 * 1024) : size_t(180 * 1024),
+                               size_t(180 * 1024)};
     // more sites first, squarer first among equals: a breadth-first path then
     // crosses fewer tile borders (measured: 8x8 beats 16x4 at 31 depth layers,
     // 8x4 beats 16x2 at 47)
