@@ -97,6 +97,25 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
+// Atomics with acquire / release semantics at GPU scope (one instruction in
+// place of a fence and a relaxed atomic).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned r;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ unsigned long long atom_add_acquire(unsigned long long *p,
+                                                             unsigned long long v) {
+    unsigned long long r;
+    asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ void atom_exch_release(unsigned long long *p, unsigned long long v) {
+    unsigned long long r;
+    asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+    (void)r;
+}
+
 // ------------------------------------------------------- tile addressing ---
 
 struct TileSmem {
@@ -414,7 +433,8 @@ __device__ __forceinline__ int eff_dir(const SolveArgs &a) {
 template <int NPT>
 __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi)[NPT],
                            const unsigned (&mk)[NPT], int first_inner = 4,
-                           int max_outer = 1 << 30) {
+                           int max_outer = 1 << 30, const unsigned *done_ctr = nullptr,
+                           unsigned items = 0, bool *cut = nullptr) {
     const TileGeom &t = a.t;
     int off[kSlots];
 #pragma unroll
@@ -431,8 +451,18 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
     constexpr int kInner = 2;
     int32_t *ht = m.ht;
     bool any_change = false;
+    // Straggler cut (with done_ctr): after a round that changed heights, stop
+    // when all but 1 + items / 8 of the step's items are done; the caller
+    // queues the tile again, and the heights so far are upper bounds of the
+    // fixed point, so a later pass resumes from them.  Thread 0 reads the
+    // done count at the start of a round and publishes its decision before
+    // the round's barrier, in a slot the next round does not overwrite.
+    __shared__ int s_rstop[2];
+    const unsigned margin = 1 + items / 8;
     for (int outer = 0;; outer++) {
         int changed = 0;
+        unsigned seen = 0;
+        if (done_ctr && threadIdx.x == 0) seen = *(volatile const unsigned *)done_ctr;
         // a first round of fewer sweeps settles tiles whose halo change does
         // not reach them without paying for a full round
         const int n_inner = outer == 0 ? first_inner : kInner;
@@ -457,9 +487,14 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
                 }
             }
         }
+        if (done_ctr && threadIdx.x == 0) s_rstop[outer & 1] = seen + margin >= items;
         if (!__syncthreads_or(changed)) break;
         any_change = true;
         if (outer + 1 >= max_outer) break;
+        if (done_ctr && s_rstop[outer & 1]) {
+            *cut = true;
+            break;
+        }
     }
     return any_change;
 }
@@ -597,7 +632,8 @@ __device__ __forceinline__ int side_tile(const TileGeom &t, const TileOrigin &o,
 template <int NPT>
 __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, int tile,
                                        int &changed, int32_t *dirty_next, int32_t *list_next,
-                                       int32_t *count_next) {
+                                       int32_t *count_next, const unsigned *done_ctr,
+                                       unsigned items) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const TileOrigin o = tile_origin(t, tile);
@@ -637,7 +673,8 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
     if (threadIdx.x == 0) s_sides = 0;
     __syncthreads();
     // one sweep first: most tiles a halo change marks need no more
-    const bool ch = relax_tile<NPT>(a, m, pi, mk, 1);
+    bool cut = false;
+    const bool ch = relax_tile<NPT>(a, m, pi, mk, 1, 1 << 30, done_ctr, items, &cut);
     int act = 0;
     unsigned sides = 0;
 #pragma unroll
@@ -659,6 +696,8 @@ __device__ long long relabel_pass_tile(const SolveArgs &a, const TileSmem &m, in
         const int nb = side_tile(t, o, tile, threadIdx.x);
         if (nb >= 0) enqueue(dirty_next, list_next, count_next, nb);
     }
+    // a relaxation cut short goes on in the next pass
+    if (cut && threadIdx.x == 4) enqueue(dirty_next, list_next, count_next, tile);
     if (ch) changed = 1;
     __syncthreads();
     if (threadIdx.x == 0) __stcg(&a.tile_cnt[tile], (int32_t)tot);
@@ -1254,9 +1293,9 @@ __device__ void pair_results(const BatchArgs &B, const PairState &st, const Solv
 __device__ void end_step(const BatchArgs &B, int p, int slot) {
     PairCtl *c = B.ctl + p;
     const SolveArgs &a = B.pair[p];
-    __threadfence();
     // the step's sums, its number, the pair's state and the queue the step
-    // filled for the next one, loaded together
+    // filled for the next one, loaded together (the caller's acquire on the
+    // done count orders them after every item's writes)
     long long v0[4];
     for (int k = 0; k < 4; k++) v0[k] = *(volatile long long *)&c->red[slot][k];
     const int32_t q0 = *(volatile int32_t *)&c->qcount[(slot + 1) % 3];
@@ -1291,8 +1330,7 @@ __device__ void end_step(const BatchArgs &B, int p, int slot) {
     c->done = 0;
     c->step = step;
     if (st.phase == PH_DONE) pair_results(B, st, a, st.status);
-    __threadfence();
-    atomicExch(&c->claim, pack_claim(step, items, 0));
+    atom_exch_release(&c->claim, pack_claim(step, items, 0));
     if (st.phase == PH_DONE) atomicAdd(&B.bar->active, 1);
 }
 
@@ -1350,11 +1388,10 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
                     PairCtl *c = B.ctl + p;
                     const unsigned long long w0 = *(volatile unsigned long long *)&c->claim;
                     if ((w0 & kItemMask) >= ((w0 >> 24) & kItemMask)) continue;
-                    const unsigned long long w = atomicAdd(&c->claim, 1ull);
+                    const unsigned long long w = atom_add_acquire(&c->claim, 1ull);
                     const unsigned items = (unsigned)((w >> 24) & kItemMask);
                     const unsigned idx = (unsigned)(w & kItemMask);
                     if (idx >= items) continue;
-                    __threadfence();
                     // everything the item needs, loaded together: the pair's
                     // state, and both ways the item may name its tile (the
                     // queued tile at this slot, or tile idx with its count)
@@ -1419,7 +1456,8 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
                 int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
                 if (pass > 1 && threadIdx.x == 0) __stcg(&dcur[tile], 0);
                 int ch = 0;
-                va = relabel_pass_tile<NPT>(a, m, tile, ch, dnext, list_next, count_next);
+                va = relabel_pass_tile<NPT>(a, m, tile, ch, dnext, list_next, count_next, &c->done,
+                                            (unsigned)s_claim[4]);
                 vb = ch;
                 vc = 1;
             } else if (phase == PH_SWEEP) {
@@ -1442,11 +1480,11 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
             if (vb) atomicAdd((unsigned long long *)&rp[1], (unsigned long long)vb);
             if (vc) atomicAdd((unsigned long long *)&rp[2], (unsigned long long)vc);
             if (ovf) atomicAdd((unsigned long long *)&rp[3], 1ull);
-            __threadfence();
             // the step's item count, as claimed (the step cannot end before
-            // this item does)
+            // this item does); the count is a release (the item's writes
+            // before it) and an acquire (every item's writes after it)
             const unsigned total = (unsigned)s_claim[4];
-            if (atomicAdd(&c->done, 1u) + 1u == total) end_step(B, pr, slot);
+            if (atom_add_acq_rel(&c->done, 1u) + 1u == total) end_step(B, pr, slot);
         }
         __syncthreads();
     }
