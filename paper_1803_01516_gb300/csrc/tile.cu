@@ -69,6 +69,7 @@ struct SolveArgs {
     int64_t *flow;       // label extraction output [1]
     int mode, sweeps_per_relabel, local_iters, relabel_passes, tail_iters;
     long long fixed_sweeps, max_iters;
+    int npt;             // own nodes per thread of the pair's tile shape (4 or 8)
 };
 
 // Every read of solver state inside the persistent kernel bypasses L1: other
@@ -110,10 +111,11 @@ __device__ __forceinline__ unsigned long long atom_add_acquire(unsigned long lon
     asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
     return r;
 }
-__device__ __forceinline__ void atom_exch_release(unsigned long long *p, unsigned long long v) {
+__device__ __forceinline__ unsigned long long atom_exch_release(unsigned long long *p,
+                                                              unsigned long long v) {
     unsigned long long r;
     asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
-    (void)r;
+    return r;
 }
 
 // ------------------------------------------------------- tile addressing ---
@@ -796,7 +798,8 @@ __device__ void build_tables(const SolveArgs &a) {
 template <int NPT, int BT>
 __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int round, int iters,
                            int &overflow, int32_t *list_next, int32_t *count_next,
-                           const unsigned *done_ctr, unsigned items) {
+                           const unsigned *done_ctr, unsigned items,
+                           uint32_t (*s_wlist)[8 * 32]) {
     const Geom &g = a.g;
     const TileGeom &t = a.t;
     const State &s = a.s;
@@ -878,7 +881,6 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     // warps (only a node's own warp lowers its excess, and residuals are
     // consumed only by an arc's tail).  Every load of a discharge depends only
     // on the list entry, so they are in flight together.
-    __shared__ uint32_t s_wlist[BT / 32][8 * 32];
     unsigned nb_touch = 0;   // bit 0: left, 1: right, 2: up, 3: down neighbour tile received flow
     const int lane = threadIdx.x & 31;
     uint32_t *wl_list = s_wlist[threadIdx.x >> 5];
@@ -1337,6 +1339,7 @@ __device__ void end_step(const BatchArgs &B, int p, int slot) {
 template <int NPT, int BT>
 __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_constant__ BatchArgs B) {
     extern __shared__ int32_t smem[];
+    __shared__ uint32_t s_wlist[BT / 32][8 * 32];   // the sweep's per-warp active lists
     // pair, item, queue slot of the step, exit flag, items of the step, the
     // queued tile at the item (speculative), the item's tile count (speculative)
     __shared__ int s_claim[7];
@@ -1442,7 +1445,10 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
         int ovf = 0;
         if (tile >= 0) {
             if (phase == PH_INIT) {
-                va = relabel_init_tile<NPT>(a, m, tile);
+                // a pair whose tiles need 4 nodes per thread runs the
+                // 4-node code also when the launch is sized for 8
+                va = (NPT == 8 && a.npt == 4) ? relabel_init_tile<4>(a, m, tile)
+                                              : relabel_init_tile<NPT>(a, m, tile);
                 vc = 1;
                 if (threadIdx.x == 0) {
                     __stcg(&a.tile_dirty[tile], 0);
@@ -1456,15 +1462,23 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
                 int32_t *dnext = a.tile_dirty + ((pass + 1) & 1) * T;
                 if (pass > 1 && threadIdx.x == 0) __stcg(&dcur[tile], 0);
                 int ch = 0;
-                va = relabel_pass_tile<NPT>(a, m, tile, ch, dnext, list_next, count_next, &c->done,
-                                            (unsigned)s_claim[4]);
+                va = (NPT == 8 && a.npt == 4)
+                         ? relabel_pass_tile<4>(a, m, tile, ch, dnext, list_next, count_next,
+                                                &c->done, (unsigned)s_claim[4])
+                         : relabel_pass_tile<NPT>(a, m, tile, ch, dnext, list_next, count_next,
+                                                  &c->done, (unsigned)s_claim[4]);
                 vb = ch;
                 vc = 1;
             } else if (phase == PH_SWEEP) {
                 const int cur = (int)(s_st.round & 1);
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
-                sweep_tile<NPT, BT>(a, m, tile, cur, s_st.tail ? a.tail_iters : a.local_iters, ovf,
-                                list_next, count_next, &c->done, (unsigned)s_claim[4]);
+                const int iters = s_st.tail ? a.tail_iters : a.local_iters;
+                if (NPT == 8 && a.npt == 4)
+                    sweep_tile<4, BT>(a, m, tile, cur, iters, ovf, list_next, count_next, &c->done,
+                                      (unsigned)s_claim[4], s_wlist);
+                else
+                    sweep_tile<NPT, BT>(a, m, tile, cur, iters, ovf, list_next, count_next,
+                                        &c->done, (unsigned)s_claim[4], s_wlist);
                 ovf = __syncthreads_or(ovf);
                 va = 1;
             } else {   // PH_LABELS
@@ -1599,6 +1613,7 @@ static int setup_args(const Geom &g, const State &s, const Work &w, const gs_sol
     a.g = g;
     a.s = s;
     if (!pick_tile(g, a.t, npt, smem, o->tile_w, o->tile_h, bt)) return GS_ERR_INVAL;
+    a.npt = npt;
     // a step's item count travels in 24 bits of the claim word
     if (a.t.T > (int)(kItemMask - 4096)) return GS_ERR_INVAL;
     char *extra = (char *)w.mark + round_up(g.N * sizeof(int32_t), 256);
