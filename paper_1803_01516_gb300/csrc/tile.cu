@@ -454,13 +454,15 @@ __device__ bool relax_tile(const SolveArgs &a, const TileSmem &m, const int (&pi
     int32_t *ht = m.ht;
     bool any_change = false;
     // Straggler cut (with done_ctr): after a round that changed heights, stop
-    // when all but 1 + items / 8 of the step's items are done; the caller
-    // queues the tile again, and the heights so far are upper bounds of the
-    // fixed point, so a later pass resumes from them.  Thread 0 reads the
-    // done count at the start of a round and publishes its decision before
-    // the round's barrier, in a slot the next round does not overwrite.
+    // when all but 1 + min(items / 8, half the grid) of the step's items are
+    // done (the last items of a step much larger than the grid are not
+    // stragglers: they started late).  The caller queues the tile again, and
+    // the heights so far are upper bounds of the fixed point, so a later pass
+    // resumes from them.  Thread 0 reads the done count at the start of a
+    // round and publishes its decision before the round's barrier, in a slot
+    // the next round does not overwrite.
     __shared__ int s_rstop[2];
-    const unsigned margin = 1 + items / 8;
+    const unsigned margin = 1 + min(items / 8, gridDim.x / 2);
     for (int outer = 0;; outer++) {
         int changed = 0;
         unsigned seen = 0;
@@ -888,12 +890,12 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     volatile int32_t *vht = m.ht;
     // Straggler cut: a step ends when its last item does, so a visit still
     // running when nearly all of its step's items are done (all but 1 +
-    // items / 8) stops after half its local iterations.  Its tile keeps its
-    // work and is queued for the next round.  Thread 0 reads the step's done
-    // count once per iteration and uses it one iteration later (the load's
-    // latency hides behind the iteration).
+    // min(items / 8, half the grid)) stops after half its local iterations.
+    // Its tile keeps its work and is queued for the next round.  Thread 0
+    // reads the step's done count once per iteration and uses it one
+    // iteration later (the load's latency hides behind the iteration).
     unsigned seen = 0;
-    const unsigned margin = 1 + items / 8;
+    const unsigned margin = 1 + min(items / 8, gridDim.x / 2);
     for (int it = 0; it < iters; it++) {
         if (threadIdx.x == 0) {
             if (it >= 2 && seen + margin >= items) s_stop = 1;
