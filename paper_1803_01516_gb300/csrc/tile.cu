@@ -893,11 +893,12 @@ __device__ void sweep_tile(const SolveArgs &a, const TileSmem &m, int tile, int 
     // min(items / 8, half the grid)) stops after half its local iterations.
     // Its tile keeps its work and is queued for the next round.  Thread 0
     // reads the step's done count once per iteration and uses it one
-    // iteration later (the load's latency hides behind the iteration).
+    // iteration later (the load's latency hides behind the iteration).  No
+    // cut without done_ctr (fixed-sweep mode: a round is a full round).
     unsigned seen = 0;
     const unsigned margin = 1 + min(items / 8, gridDim.x / 2);
     for (int it = 0; it < iters; it++) {
-        if (threadIdx.x == 0) {
+        if (done_ctr && threadIdx.x == 0) {
             if (it >= 2 && seen + margin >= items) s_stop = 1;
             seen = *(volatile const unsigned *)done_ctr;
         }
@@ -1475,12 +1476,13 @@ __global__ void __launch_bounds__(BT, BT == 256 ? 2 : 1) k_batch(const __grid_co
                 const int cur = (int)(s_st.round & 1);
                 if (threadIdx.x == 0) __stcg(&a.tile_act[cur * T + tile], 0);
                 const int iters = s_st.tail ? a.tail_iters : a.local_iters;
+                const unsigned *done_ctr = a.mode == GS_MODE_FIXED_SWEEPS ? nullptr : &c->done;
                 if (NPT == 8 && a.npt == 4)
-                    sweep_tile<4, BT>(a, m, tile, cur, iters, ovf, list_next, count_next, &c->done,
+                    sweep_tile<4, BT>(a, m, tile, cur, iters, ovf, list_next, count_next, done_ctr,
                                       (unsigned)s_claim[4], s_wlist);
                 else
                     sweep_tile<NPT, BT>(a, m, tile, cur, iters, ovf, list_next, count_next,
-                                        &c->done, (unsigned)s_claim[4], s_wlist);
+                                        done_ctr, (unsigned)s_claim[4], s_wlist);
                 ovf = __syncthreads_or(ovf);
                 va = 1;
             } else {   // PH_LABELS
