@@ -109,18 +109,29 @@ def _time_config(p: gc.Params, pairs, cfg, reps: int = 2) -> float:
     return ts[len(ts) // 2]
 
 
-def tune(p: gc.Params, n_pairs: int = 2, save: bool = True) -> dict:
+def tune(p: gc.Params, n_pairs: int = 2, save: bool = True, pairs=None) -> dict:
     """Tile shape and block size first (default schedule), then the schedule on
-    the best of those, each measured on synthetic pairs of p's size.  An entry
-    is [sweeps_per_relabel, local_iters, relabel_passes, tile_w, tile_h,
+    the best of those, each measured on `pairs` -- the caller's own image
+    pairs of p's size, a list of (left, right) uint8 device tensors -- or, by
+    default, on n_pairs synthetic pairs of that size.  An entry is
+    [sweeps_per_relabel, local_iters, relabel_passes, tile_w, tile_h,
     tail_iters, cta_threads]."""
-    wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
-                        scene="layers", n_layers=5, n_slanted=2,
-                        max_disp=min(2 * (p.D - 1), 40), seed_base=77)
-    pairs = []
-    for i in range(n_pairs):
-        L, R, _ = synth.make_pair(wl, i)
-        pairs.append((torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()))
+    if pairs is None:
+        wl = synth.Workload(f"tune-{bucket(p)}", p.w, p.h, p.D, tau=30, lam=p.lam, sigma=2.0,
+                            scene="layers", n_layers=5, n_slanted=2,
+                            max_disp=min(2 * (p.D - 1), 40), seed_base=77)
+        pairs = []
+        for i in range(n_pairs):
+            L, R, _ = synth.make_pair(wl, i)
+            pairs.append((torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()))
+    else:
+        pairs = list(pairs)
+        if not pairs:
+            raise ValueError("tune: no pairs to measure on")
+        for L, R in pairs:
+            if tuple(L.shape) != (p.h, p.w) or tuple(R.shape) != (p.h, p.w):
+                raise ValueError(f"tune: pair of shape {tuple(L.shape)} / {tuple(R.shape)}, "
+                                 f"expected {(p.h, p.w)}")
     results = {}
     for tw, th in SHAPES:
         for bt in CTA_THREADS:

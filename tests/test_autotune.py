@@ -68,3 +68,36 @@ def test_block_size_entry(tune):
     # 512 threads (the default) take the larger tile
     info = gc.gs_tile_info(p, gc.SolveOpts())
     assert info["tile_w"] * info["tile_h"] > 64
+
+
+def test_tune_on_callers_pairs(tune, monkeypatch):
+    """tune() measures on the caller's own pairs when given (shapes checked),
+    keeps the fastest configuration of both stages and caches it under the
+    size bucket.  The timer is replaced by a host-side cost model here."""
+    import torch
+    from paper_1803_01516_gb300 import gazecut as gc
+    p = gc.Params(w=100, h=40, D=8, tau=30, lam=10)
+    mine = [(torch.zeros(40, 100, dtype=torch.uint8), torch.zeros(40, 100, dtype=torch.uint8))]
+    seen = []
+
+    def fake_time(pp, pairs, cfg, reps=2):
+        seen.append(pairs)
+        spr, li, rp, tw, th = cfg[:5]
+        ti = cfg[5] if len(cfg) > 5 else 0
+        bt = cfg[6] if len(cfg) > 6 else 0
+        # fastest: 8x4 tiles on 256 threads, then 32 sweeps per relabel, 4
+        # local iterations, 8 passes, tail 8
+        return (abs(tw - 8) + abs(th - 4) + (bt != 256) + abs(spr - 32) / 8 + abs(li - 4)
+                + abs(rp - 8) / 4 + abs(ti - 8) / 4)
+
+    monkeypatch.setattr(tune, "_time_config", fake_time)
+    e = tune.tune(p, pairs=mine)
+    assert e["best"] == [32, 4, 8, 8, 4, 8, 256]
+    assert all(s == mine for s in seen) and len(seen) > 10
+    o = tune.tuned_opts(p)
+    assert (o.sweeps_per_relabel, o.local_iters, o.relabel_passes, o.tile_w, o.tile_h,
+            o.tail_iters, o.cta_threads) == (32, 4, 8, 8, 4, 8, 256)
+    with pytest.raises(ValueError):
+        tune.tune(p, pairs=[(torch.zeros(40, 99, dtype=torch.uint8),) * 2])
+    with pytest.raises(ValueError):
+        tune.tune(p, pairs=[])
