@@ -101,3 +101,21 @@ def test_tune_on_callers_pairs(tune, monkeypatch):
         tune.tune(p, pairs=[(torch.zeros(40, 99, dtype=torch.uint8),) * 2])
     with pytest.raises(ValueError):
         tune.tune(p, pairs=[])
+
+
+def test_block_size_shapes_fit_every_depth_range(tune):
+    """With 256-thread blocks the library's own tile fits two blocks' shared
+    memory in an SM up to 64 depth numbers and falls back to one block per SM
+    for longer chains; explicit shapes keep the one-block budget."""
+    from paper_1803_01516_gb300 import gazecut as gc
+    for D in (4, 16, 33, 64, 128, 200):
+        p = gc.Params(w=2 * (D - 1) + 200, h=120, D=D, tau=30, lam=10)
+        info = gc.gs_tile_info(p, gc.SolveOpts(cta_threads=256))
+        assert info["smem_bytes"] <= 180 * 1024
+        if D <= 64:
+            assert info["smem_bytes"] <= 80 * 1024, (D, info)
+        # a tile's own nodes: at most 8 per thread of the 256
+        assert info["tile_w"] * info["tile_h"] * (D - 1) <= 8 * 256
+    p = gc.Params(w=384, h=288, D=16, tau=30, lam=10)
+    info = gc.gs_tile_info(p, gc.SolveOpts(cta_threads=256, tile_w=16, tile_h=8))
+    assert (info["tile_w"], info["tile_h"]) == (16, 8) and info["smem_bytes"] > 80 * 1024
